@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark: dynamic max-flow repair on an RMAT scale-20 graph (GB300).
+
+Workload (one GPU): RMAT power-law graph, 2^20 vertices, 16.7M directed edges
+(a, b, c, d = 0.57, 0.19, 0.19, 0.05), int32 capacities U[1, 1000], s and t the
+two vertices of highest out-degree.  One step = one mixed batch of
+--batch distinct uniformly chosen edges (half +U[1,500], half -U[1,500]
+clamped at 0) applied to the resident residual graph and repaired by the
+dynamic push-relabel kernel (validate, apply, clamp, re-saturate, then BFS /
+push-relabel / remove-invalid until no vertex is active).
+
+value      batches repaired per second, batch already resident in HBM,
+           device time of the repair kernel (CUDA events, L2 flushed between
+           steps by writing a 512 MiB buffer outside the timed region)
+e2e        the same through the C ABI with pinned HOST batch buffers: the
+           host->device batch copy, the repair and the device->host read of the
+           flow value and status are inside the timed region
+sizes      dynamic repair vs static GPU recompute (solve from zero flow on the
+           same capacities) for 1k / 10k / 100k / 1M-edge batches
+roofline   algorithmic bytes of the repair kernel (per-unit figures x device
+           counters) / its measured duration / measured HBM peak
+cpu_baseline  the CPU oracle (FIFO push-relabel, from scratch) on a bounded
+           sample of the same batches, timed on this host
+
+--impl reference runs that oracle arm alone.  Under torchrun every rank runs an
+independent replica of the workload on its own GPU (the method has no
+exchange step); value = batches of all ranks / max over ranks of the time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import generators as gen  # noqa: E402
+
+METRIC = "update-batch latency & speedup vs static GPU push-relabel; HBM GB/s frac"
+UNIT = "batches/s"
+SCALE = 20
+SEED = 1
+
+# Algorithmic bytes per unit of work of the repair kernel (the design doc lists the
+# same figures with their derivation).
+BYTES = {
+    "bfs_arcs": 12,       # head 4 + mirrored residual 4 + height of the head 4
+    "bfs_vertices": 20,   # row offsets 8 + height write 4 + queue write 4 + queue read 4
+    "height_init": 12,    # per vertex per BFS: excess 8 + height write 4
+    "pr_arcs": 12,        # residual 4 + head 4 + height of the head 4
+    "pushes": 64,         # 4 int32 residual RMW (8 each) + 2 int64 excess RMW (16 each)
+    "relabels": 4,
+    "ri_arcs": 12,
+    "ri_moves": 64,
+    "worklist": 8,        # worklist write + read
+    "batch": 64,          # id+cap 8, cap_edge RMW 8, arc map 4, stamp RMW 8, cap/r/rr RMW 24, scratch 12
+    "clamped": 48,
+    "resat_arcs": 4,
+}
+
+
+def algorithmic_bytes(st: dict, n: int) -> int:
+    b = 0
+    for k, w in BYTES.items():
+        if k == "height_init":
+            b += w * n * (st["iterations"] + 1)
+        else:
+            b += w * st[k]
+    return int(b)
+
+
+def kernel_source_hash() -> str:
+    p = os.path.join(ROOT, "paper_2511_05895_gb300", "csrc", "mf_gpu.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel_hash: str):
+    """DRAM bytes per launch of k_solve from the committed ncu summary, if it
+    was taken on this exact kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "k_solve_rmat20_batch100k.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", txt)
+    t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9]+)", txt)
+    if h and t and h.group(1) == kernel_hash:
+        return int(t.group(1))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [ln.split(",") for ln in open(self.path).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names[1:], r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_batches(cap: np.ndarray, k: int, count: int, index0: int):
+    out = []
+    for i in range(count):
+        b = gen.mixed_batch(cap, k, 1, 500, seed=SEED, index=index0 + i)
+        gen.apply_batch(cap, b)
+        out.append(b)
+    return out
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    """The oracle arm: FIFO push-relabel from scratch after each batch."""
+    if rank != 0:
+        return
+    import oracle
+    g = gen.rmat(scale=SCALE, seed=SEED)
+    cap = g.cap.copy()
+    batches = make_batches(cap.copy(), args.batch, args.warmup + args.steps, 10_000)
+    cur = g.cap.copy()
+    times = []
+    for i, b in enumerate(batches):
+        gen.apply_batch(cur, b)
+        t0 = time.perf_counter()
+        oracle.maxflow_fifo(g.n, g.row_ptr, g.col, cur, g.s, g.t)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": workload_config(args, g),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{len(times)} consecutive {args.batch}-edge mixed batches, "
+                                   "FIFO push-relabel from scratch per batch, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, g) -> dict:
+    return {"workload": f"RMAT scale {SCALE} (n={g.n}, m={g.m}, a=0.57 b=0.19 c=0.19), caps U[1,1000], "
+                        f"mixed batches of {args.batch} edges (+/-U[1,500])",
+            "n": g.n, "m": g.m, "batch_edges": args.batch, "seed": SEED,
+            "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=100_000)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-sizes", action="store_true", help="skip the per-size dynamic/static comparison")
+    ap.add_argument("--cpu-sample", type=int, default=3, help="batches in the CPU-oracle sample")
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2511_05895_gb300 import MaxFlowGraph
+
+    g = gen.rmat(scale=SCALE, seed=SEED + 1000 * rank)
+    cap = g.cap.copy()
+    G = MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t)
+    G.solve()
+    flow0 = G.flow_value()
+
+    host_cap = cap.copy()
+    batches = make_batches(host_cap, args.batch, args.warmup + args.steps, 0)
+    dev = [(torch.from_numpy(b.edge_id).cuda(), torch.from_numpy(b.new_cap).cuda()) for b in batches]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed_step(ids, caps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.apply_updates(ids, caps)
+        e1.record(stream)
+        return e0, e1
+
+    for i in range(args.warmup):
+        timed_step(*dev[i])
+    G.sync()
+    stats_acc = {k: 0 for k in list(BYTES) + ["iterations"]}
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    events, per_step_bytes = [], []
+    for i in range(args.warmup, args.warmup + args.steps):
+        ev = timed_step(*dev[i])
+        events.append(ev)
+        # device counters of this launch (read after it completes; outside the timing)
+        ev[1].synchronize()
+        st = G.stats()
+        per_step_bytes.append(algorithmic_bytes(st, g.n))
+        for k in stats_acc:
+            stats_acc[k] += st[k]
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in events]          # ms
+    t_total = sum(times) / 1000.0
+    if dist:
+        tt = torch.tensor([t_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+        dist.barrier()
+    G.sync()
+    flow_after = G.flow_value()
+
+    # certificate of the final state (optimality proof; no oracle needed)
+    import oracle
+    from tests._helpers import certify_gpu
+    certified = True
+    try:
+        certify_gpu(G, g, host_cap, flow_after)
+    except AssertionError:
+        certified = False
+
+    # ---- e2e through the C ABI with pinned host buffers ------------------
+    e2e_batches = make_batches(host_cap, args.batch, args.steps, 5_000)
+    pinned = [(torch.from_numpy(b.edge_id).pin_memory(), torch.from_numpy(b.new_cap).pin_memory()) for b in e2e_batches]
+    torch.cuda.synchronize()
+    t_e2e = 0.0
+    for ids, caps in pinned:
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.apply_updates(ids, caps)
+        G.flow_value()
+        t_e2e += time.perf_counter() - t0
+    e2e_value = world * args.steps / t_e2e if world == 1 else None
+    if dist:
+        tt = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_value = world * args.steps / float(tt.item())
+
+    # ---- dynamic vs static recompute per batch size ----------------------
+    sizes = {}
+    if not args.no_sizes:
+        empty = (torch.zeros(0, dtype=torch.int32, device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"))
+        for j, k in enumerate((1_000, 10_000, 100_000, 1_000_000)):
+            bs = make_batches(host_cap, k, 3, 20_000 + 10 * j)
+            dyn, sta = [], []
+            for b in bs:
+                ids = torch.from_numpy(b.edge_id).cuda()
+                cp = torch.from_numpy(b.new_cap).cuda()
+                a0, a1 = timed_step(ids, cp)
+                a1.synchronize()
+                dyn.append(a0.elapsed_time(a1))
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.zero_()
+                s0.record(stream)
+                G.apply_updates(empty[0], empty[1], recompute=True)    # static recompute, same caps
+                s1.record(stream)
+                s1.synchronize()
+                sta.append(s0.elapsed_time(s1))
+            G.sync()
+            d, s = statistics.median(dyn), statistics.median(sta)
+            sizes[str(k)] = {"dynamic_ms": round(d, 4), "static_recompute_ms": round(s, 4),
+                             "speedup": round(s / d, 3), "frac_of_edges": round(k / g.m, 6)}
+
+    # ---- CPU oracle on a bounded sample ----------------------------------
+    cpu = None
+    if rank == 0 and world >= 1 and args.cpu_sample > 0:
+        cur = g.cap.copy()
+        cpu_batches = make_batches(g.cap.copy(), args.batch, args.cpu_sample, 0)
+        dt = 0.0
+        for b in cpu_batches:
+            gen.apply_batch(cur, b)
+            t0 = time.perf_counter()
+            oracle.maxflow_fifo(g.n, g.row_ptr, g.col, cur, g.s, g.t)
+            dt += time.perf_counter() - t0
+        cpu = {"value": args.cpu_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sample} recomputes from scratch (FIFO push-relabel, 1 thread) "
+                         f"of the RMAT-20 graph after {args.batch}-edge batches"}
+
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    mean_ms = 1000.0 * sum(times) / 1000.0 / len(times)
+    mean_bytes = sum(per_step_bytes) / len(per_step_bytes)
+    achieved = mean_bytes / (mean_ms / 1000.0) / 1e9
+    khash = kernel_source_hash()
+    traffic = recorded_traffic(khash)
+    value = world * args.steps / t_total
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": workload_config(args, g),
+        "latency_ms": {"p50": statistics.median(times), "p99": float(np.percentile(times, 99)),
+                       "min": min(times), "max": max(times)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": peak_src, "kernel": "k_solve",
+                     "algorithmic_bytes_per_launch": int(mean_bytes), "kernel_source": khash},
+        "counters_per_step": {k: v / args.steps for k, v in stats_acc.items()},
+        "sizes": sizes,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * args.batch,
+                "d2h_bytes_per_step": 16},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "checks": {"flow_initial": flow0, "flow_final": flow_after, "certified": certified},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,1016 @@
+// GB300 (sm_103a) dynamic max-flow: device kernels and the C ABI of mf.h.
+//
+// The whole solve / repair of one graph is ONE persistent cooperative kernel
+// (k_solve): every CTA of one full wave runs the phases below in lock-step,
+// separated by a bounded grid barrier, so the data-dependent loops (BFS
+// levels, the push/relabel rounds) never return to the host (the paper keeps
+// termination on the GPU "without CPU intervention", Sec. 3):
+//
+//   validate batch -> apply capacity changes (Alg. 5, lines 1-3)
+//   -> clamp negative residuals (Alg. 5, lines 4-11)
+//   -> saturate source arcs (Alg. 4 lines 3-7 / Alg. 1 third loop)
+//   -> loop { height init with deficient vertices as sinks (Alg. 4)
+//             backward BFS global relabel + active worklist (Sec. 5.3)
+//             stop when no vertex is active
+//             PushRelabel x KERNELCYCLES (Alg. 2)
+//             RemoveInvalidEdges (Alg. 3) }
+//   -> flow = e(t) + sum of deficits (Alg. 4, final sum).
+//
+// Residual capacities are kept twice: r[a] and its mirror rr[a] = r[rev[a]],
+// so that the backward BFS reads the residual of the arc INTO the frontier
+// vertex from a contiguous array instead of gathering r[rev[a]].  Every write
+// to r[x] has a matching write to rr[rev[x]].
+//
+// Mutable arrays are read with ld.global.cg (L2, coherent across SMs): the
+// persistent kernel never relies on L1 contents across a grid barrier.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mf.h"
+#include "mf_internal.h"
+
+namespace mf {
+
+constexpr int kBlock = 256;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kWaitNs = 20ull * 1000ull * 1000ull * 1000ull;  // 20 s per barrier wait
+
+// status bits (Ctl::status)
+constexpr int ST_EINVAL = 1;   // rejected batch (state unchanged)
+constexpr int ST_ITERS = 2;    // max_iters reached
+constexpr int ST_WAIT = 4;     // a grid-barrier wait reached its time limit
+constexpr int ST_STICKY = ST_ITERS | ST_WAIT;
+
+enum JobKind { JOB_SOLVE = 0, JOB_REPAIR = 1, JOB_RECOMPUTE = 2 };
+
+// Device control block.  Fields marked (z) are zero whenever no k_solve is
+// running: they are zeroed at creation, by mf_solve, and by the last thread
+// of every k_solve that ends normally.
+struct Ctl {
+    int status;           // ST_* bits                      } read together by
+    int batch_err;        // (z) set by batch validation    } mf_flow_value
+    long long flow;       // result of the last solve/repair }
+    unsigned bar_count;   // grid barrier arrivals (z)
+    unsigned bar_gen;     // grid barrier generation
+    int qcnt[3];          // (z) BFS frontier sizes, rotating by level
+    int ccnt[3];          // (z) BFS chunk-item counts, rotating by level
+    int wcnt;             // (z) active worklist size
+    int pad0;
+    long long dacc[2];    // (z) sum of deficits at the last height init
+    long long iters;
+    long long st[12];     // statistics, see enum Stat
+};
+
+enum Stat {
+    S_LEVELS, S_BFS_VERTS, S_BFS_ARCS, S_WL, S_PR_ARCS, S_PUSH, S_RELABEL, S_RI_ARCS, S_RI_MOVES,
+    S_BATCH, S_CLAMPED, S_RESAT, S_COUNT
+};
+
+struct DevGraph {
+    int n, s, t, m;
+    long long A;
+    int cap_limit;
+    const int *row, *head, *rev, *arc_of_edge;
+    int *cap, *r, *rr, *h, *cap_edge;
+    long long *e;
+    unsigned *stamp;
+    int *qb0, *qb1, *wl;
+    int2 *cb;
+    Ctl *ctl;
+};
+
+struct Job {
+    int kind, k, flags, kc;
+    unsigned seq;
+    long long max_iters;
+    const int *ids, *caps;
+    int *newc, *dlt;
+};
+
+// ---------------------------------------------------------------- helpers --
+__device__ __forceinline__ int lcg(const int *p) { return __ldcg(p); }
+__device__ __forceinline__ long long lcg(const long long *p) { return __ldcg(p); }
+__device__ __forceinline__ int2 lcg(const int2 *p) { return __ldcg(p); }
+
+__device__ __forceinline__ void add_ll(long long *p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ long long warp_sum(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_min(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(kFull, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// Warp-aggregated append: one atomicAdd per warp (Sec. 5.3: ballot, then the
+// warp leader reserves space).  Must be called by all 32 lanes.
+__device__ __forceinline__ void warp_append(bool pred, int val, int *cnt, int *buf) {
+    const unsigned mask = __ballot_sync(kFull, pred);
+    if (!mask) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(mask));
+    base = __shfl_sync(kFull, base, leader);
+    if (pred) buf[base + __popc(mask & ((1u << lane) - 1u))] = val;
+}
+
+// Bounded grid barrier for a cooperative (co-resident) grid.  Returns false
+// when any CTA gave up waiting (the kernel must then return).
+__device__ bool grid_sync(Ctl *C) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned gen = ld_acquire(&C->bar_gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&C->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&C->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&C->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = gtimer();
+            unsigned spins = 0;
+            while (ld_acquire(&C->bar_gen) == gen) {
+                if ((++spins & 31u) == 0) {
+                    if (__ldcg(&C->status) & ST_WAIT) break;
+                    if (gtimer() - t0 > kWaitNs) {
+                        atomicOr(&C->status, ST_WAIT);
+                        break;
+                    }
+                }
+                __nanosleep(40);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return (__ldcg(&C->status) & ST_WAIT) == 0;
+}
+
+// ---------------------------------------------------------- BFS visiting --
+struct Counters {
+    long long bfs_arcs = 0, bfs_verts = 0, pr_arcs = 0, push = 0, relabel = 0, ri_arcs = 0,
+              ri_moves = 0, clamped = 0, resat = 0;
+};
+
+// Backward BFS step over arc a of frontier vertex u (a in u's list, head v):
+// the arc v -> u is residual iff rr[a] > 0; an unvisited v (height n) gets
+// height L + 1 (global relabel, Sec. 2.2).  Newly reached vertices with
+// positive excess are active and join the worklist.  All 32 lanes call.
+__device__ __forceinline__ void bfs_visit(const DevGraph &G, bool valid, int a, int L, int *ncnt,
+                                          int *NF, Counters &K) {
+    bool disc = false;
+    int v = 0;
+    if (valid) {
+        v = __ldg(&G.head[a]);
+        const int rin = lcg(&G.rr[a]);
+        const int hv = lcg(&G.h[v]);
+        ++K.bfs_arcs;
+        if (rin > 0 && hv == G.n && v != G.s) disc = (atomicCAS(&G.h[v], G.n, L + 1) == G.n);
+    }
+    warp_append(disc, v, ncnt, NF);
+    const bool act = disc && lcg(&G.e[v]) > 0;
+    warp_append(act, v, &G.ctl->wcnt, G.wl);
+    if (disc) ++K.bfs_verts;
+}
+
+// Expand up to 32 frontier vertices (one per lane, degree deg starting at
+// arc beg) with the arcs balanced over the lanes: lane i handles arc
+// k0 + i of the concatenated lists.
+__device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int deg, int L,
+                                                int *ncnt, int *NF, Counters &K) {
+    const int lane = threadIdx.x & 31;
+    int incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - deg;
+    for (int k0 = 0; k0 < total; k0 += 32) {
+        const int k = k0 + lane;
+        int j = 0;  // owner lane: largest j with excl_j <= k
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int cand = j + step;
+            const int ex = __shfl_sync(kFull, excl, cand & 31);
+            if (cand < 32 && ex <= k) j = cand;
+        }
+        const int ob = __shfl_sync(kFull, beg, j);
+        const int oe = __shfl_sync(kFull, excl, j);
+        bfs_visit(G, k < total, ob + (k - oe), L, ncnt, NF, K);
+    }
+}
+
+// ------------------------------------------------------ push / relabel --
+// Algorithm 2 on vertex u by one warp: up to kc times, find the lowest
+// residual neighbour (ties: lowest arc), then push min(e, c_f) to it with
+// atomics, or relabel u to one above it.  Neighbour heights are read once per
+// step (Note 3 of Sec. 3).  A vertex without residual arcs gets height n.
+__device__ void push_relabel_warp(const DevGraph &G, int u, int kc, Counters &K) {
+    const int lane = threadIdx.x & 31;
+    const int n = G.n;
+    const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
+    for (int c = 0; c < kc; ++c) {
+        // lane 0 reads h(u) and e(u) once; the warp follows its copy
+        int hu = 0;
+        long long eu = 0;
+        if (lane == 0) {
+            hu = lcg(&G.h[u]);
+            eu = lcg(&G.e[u]);
+        }
+        hu = __shfl_sync(kFull, hu, 0);
+        eu = __shfl_sync(kFull, eu, 0);
+        if (hu >= n || eu <= 0) break;
+        unsigned long long best = ~0ull;
+        for (int a = beg + lane; a < end; a += 32) {
+            const int ra = lcg(&G.r[a]);
+            ++K.pr_arcs;
+            if (ra > 0) {
+                const unsigned hv = (unsigned)lcg(&G.h[__ldg(&G.head[a])]);
+                const unsigned long long key = ((unsigned long long)hv << 32) | (unsigned)(a - beg);
+                best = key < best ? key : best;
+            }
+        }
+        best = warp_min(best);
+        if (lane == 0) {
+            if (best == ~0ull) {
+                G.h[u] = n;
+                ++K.relabel;
+            } else {
+                const int hh = (int)(best >> 32);
+                const int a = beg + (int)(best & 0xffffffffu);
+                if (hu > hh) {
+                    const int ra = lcg(&G.r[a]);
+                    const long long d = eu < (long long)ra ? eu : (long long)ra;
+                    if (d > 0) {
+                        const int v = __ldg(&G.head[a]);
+                        const int b = __ldg(&G.rev[a]);
+                        const int di = (int)d;
+                        atomicSub(&G.r[a], di);
+                        atomicSub(&G.rr[b], di);
+                        atomicAdd(&G.r[b], di);
+                        atomicAdd(&G.rr[a], di);
+                        add_ll(&G.e[u], -d);
+                        add_ll(&G.e[v], d);
+                        ++K.push;
+                    }
+                } else {
+                    G.h[u] = hh + 1;
+                    ++K.relabel;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Algorithm 3 on vertex u by one warp: every residual arc u -> v with
+// h(u) > h(v) + 1 is saturated, moving its residual as excess to v.
+__device__ void remove_invalid_warp(const DevGraph &G, int u, Counters &K) {
+    const int lane = threadIdx.x & 31;
+    const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
+    const int hu = __shfl_sync(kFull, lane == 0 ? lcg(&G.h[u]) : 0, 0);
+    for (int a = beg + lane; a < end; a += 32) {
+        const int ra = lcg(&G.r[a]);
+        ++K.ri_arcs;
+        if (ra > 0) {
+            const int v = __ldg(&G.head[a]);
+            if (hu > lcg(&G.h[v]) + 1) {
+                const int b = __ldg(&G.rev[a]);
+                atomicSub(&G.r[a], ra);
+                atomicSub(&G.rr[b], ra);
+                atomicAdd(&G.r[b], ra);
+                atomicAdd(&G.rr[a], ra);
+                add_ll(&G.e[u], -(long long)ra);
+                add_ll(&G.e[v], (long long)ra);
+                ++K.ri_moves;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ the kernel --
+__global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
+    Ctl *C = G.ctl;
+    const int lane = threadIdx.x & 31;
+    const long long gtid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    const long long gthreads = (long long)gridDim.x * kBlock;
+    const int gwarp = (int)(gtid >> 5);
+    const int nwarps = (int)(gthreads >> 5);
+    const int n = G.n, s = G.s, t = G.t;
+    Counters K;
+
+    // A sticky error (iteration cap, barrier wait) invalidates the state
+    // until the next mf_solve, which clears it before launching.
+    if (__ldcg(&C->status) & ST_STICKY) return;
+    if (gtid == 0) {
+        for (int i = 0; i < S_COUNT; ++i) C->st[i] = 0;
+        C->st[S_BATCH] = J.kind == JOB_SOLVE ? 0 : J.k;
+    }
+
+    // ---- batch: validate, then apply (Algorithm 5) ----------------------
+    if (J.kind != JOB_SOLVE) {
+        for (long long i = gtid; i < J.k; i += gthreads) {
+            const int eid = J.ids[i];
+            bool bad = eid < 0 || eid >= G.m;
+            int nc = 0;
+            if (!bad) {
+                long long v = J.caps[i];
+                if (J.flags & MF_DELTA) {
+                    v += lcg(&G.cap_edge[eid]);
+                    if (v < 0) v = 0;
+                }
+                if (v < 0 || v > G.cap_limit) bad = true;
+                else nc = (int)v;
+                if (atomicExch(&G.stamp[eid], J.seq) == J.seq) bad = true;  // duplicate id
+            }
+            J.newc[i] = nc;
+            if (bad) atomicOr(&C->batch_err, 1);
+        }
+        if (!grid_sync(C)) return;
+        if (lcg(&C->batch_err)) {
+            grid_sync(C);
+            if (gtid == 0) {
+                atomicOr(&C->status, ST_EINVAL);
+                C->batch_err = 0;
+            }
+            return;
+        }
+        // c_f(u,v) += c'(u,v) - c(u,v)  (Alg. 5, lines 1-3)
+        for (long long i = gtid; i < J.k; i += gthreads) {
+            const int eid = J.ids[i];
+            const int nc = lcg(&J.newc[i]);
+            const int d = nc - lcg(&G.cap_edge[eid]);
+            G.cap_edge[eid] = nc;
+            J.dlt[i] = d;
+            const int a = __ldg(&G.arc_of_edge[eid]);
+            if (a >= 0 && d != 0) {
+                atomicAdd(&G.cap[a], d);
+                if (J.kind == JOB_REPAIR) {
+                    atomicAdd(&G.r[a], d);
+                    atomicAdd(&G.rr[__ldg(&G.rev[a])], d);
+                }
+            }
+        }
+        if (!grid_sync(C)) return;
+        if (J.kind == JOB_REPAIR) {
+            // flow above the new capacity goes back: the tail keeps it as
+            // excess, the head becomes deficient (Alg. 5, lines 4-11; the
+            // excess update is the exact incremental form of Alg. 4 line 2).
+            for (long long i = gtid; i < J.k; i += gthreads) {
+                if (lcg(&J.dlt[i]) >= 0) continue;
+                const int a = __ldg(&G.arc_of_edge[J.ids[i]]);
+                if (a < 0) continue;
+                const int old = atomicMax(&G.r[a], 0);
+                if (old < 0) {
+                    const int o = -old;
+                    const int b = __ldg(&G.rev[a]);
+                    atomicAdd(&G.rr[b], o);
+                    atomicSub(&G.r[b], o);
+                    atomicSub(&G.rr[a], o);
+                    add_ll(&G.e[__ldg(&G.head[b])], (long long)o);
+                    add_ll(&G.e[__ldg(&G.head[a])], -(long long)o);
+                    ++K.clamped;
+                }
+            }
+            if (!grid_sync(C)) return;
+        }
+    }
+
+    // ---- zero flow (Algorithm 1, first two loops) ------------------------
+    if (J.kind != JOB_REPAIR) {
+        for (long long a = gtid; a < G.A; a += gthreads) {
+            G.r[a] = lcg(&G.cap[a]);
+            G.rr[a] = lcg(&G.cap[__ldg(&G.rev[a])]);
+        }
+        for (long long v = gtid; v < n; v += gthreads) G.e[v] = 0;
+        if (!grid_sync(C)) return;
+    }
+
+    // ---- saturate the source arcs (Alg. 1 third loop, Alg. 4 lines 3-7) --
+    {
+        long long moved = 0;
+        const int a0 = __ldg(&G.row[s]), a1 = __ldg(&G.row[s + 1]);
+        for (long long a = a0 + gtid; a < a1; a += gthreads) {
+            const int ra = lcg(&G.r[a]);
+            ++K.resat;
+            if (ra > 0) {
+                const int b = __ldg(&G.rev[a]);
+                G.r[a] = 0;
+                G.rr[b] = 0;
+                atomicAdd(&G.r[b], ra);
+                atomicAdd(&G.rr[a], ra);
+                add_ll(&G.e[__ldg(&G.head[a])], (long long)ra);
+                moved += ra;
+            }
+        }
+        moved = warp_sum(moved);
+        if (lane == 0 && moved) add_ll(&G.e[s], -moved);
+        if (!grid_sync(C)) return;
+    }
+
+    // ---- device loop (Algorithm 4 while-loop) ----------------------------
+    long long it = 0;
+    for (;; ++it) {
+        const int par = (int)(it & 1);
+        // height init: t and deficient vertices are sinks (height 0), all
+        // others n; the sinks form BFS level 0.
+        if (gtid == 0) {
+            C->qcnt[1] = 0;
+            C->qcnt[2] = 0;
+            C->ccnt[0] = 0;
+            C->wcnt = 0;
+            C->dacc[par ^ 1] = 0;
+        }
+        {
+            long long dsum = 0;
+            for (long long vb = (long long)gwarp * 32; vb < n; vb += gthreads) {
+                const long long v = vb + lane;
+                bool root = false;
+                if (v < n) {
+                    const long long ev = lcg(&G.e[v]);
+                    root = (v == t) || (v != s && ev < 0);
+                    G.h[v] = root ? 0 : n;
+                    if (root && v != t) dsum += ev;
+                }
+                warp_append(root, (int)v, &C->qcnt[0], G.qb0);
+            }
+            dsum = warp_sum(dsum);
+            if (lane == 0 && dsum) add_ll(&C->dacc[par], dsum);
+        }
+        if (!grid_sync(C)) return;
+
+        // backward BFS from the sinks over residual arcs (global relabel)
+        int L = 0;
+        for (;;) {
+            const int cur = lcg(&C->qcnt[L % 3]);
+            if (cur == 0) break;
+            const int *F = (L & 1) ? G.qb1 : G.qb0;
+            int *NF = (L & 1) ? G.qb0 : G.qb1;
+            int *ncnt = &C->qcnt[(L + 1) % 3];
+            int *ccnt = &C->ccnt[L % 3];
+            if (gtid == 0) {
+                C->qcnt[(L + 2) % 3] = 0;
+                C->ccnt[(L + 1) % 3] = 0;
+            }
+            for (int base = gwarp * 32; base < cur; base += nwarps * 32) {
+                const int idx = base + lane;
+                int beg = 0, deg = 0;
+                if (idx < cur) {
+                    const int u = lcg(&F[idx]);
+                    beg = __ldg(&G.row[u]);
+                    deg = __ldg(&G.row[u + 1]) - beg;
+                    if (deg > kBigDeg) {
+                        const int nc = (deg + kChunk - 1) / kChunk;
+                        const int pos = atomicAdd(ccnt, nc);
+                        for (int c = 0; c < nc; ++c) G.cb[pos + c] = make_int2(u, beg + c * kChunk);
+                        deg = 0;
+                    }
+                }
+                bfs_expand_warp(G, beg, deg, L, ncnt, NF, K);
+            }
+            if (!grid_sync(C)) return;
+            const int nch = lcg(ccnt);
+            if (nch > 0) {
+                for (int c = gwarp; c < nch; c += nwarps) {
+                    const int2 item = lcg(&G.cb[c]);
+                    const int a1 = min(item.y + kChunk, __ldg(&G.row[item.x + 1]));
+                    for (int ab = item.y; ab < a1; ab += 32) bfs_visit(G, ab + lane < a1, ab + lane, L, ncnt, NF, K);
+                }
+                if (!grid_sync(C)) return;
+            }
+            ++L;
+        }
+        if (gtid == 0) C->st[S_LEVELS] += L;
+
+        // termination: no active vertex under the fresh BFS heights
+        const int nw = lcg(&C->wcnt);
+        if (nw == 0) break;
+        if (it >= J.max_iters) {
+            if (gtid == 0) atomicOr(&C->status, ST_ITERS);
+            break;
+        }
+        if (gtid == 0) C->st[S_WL] += nw;
+
+        // PushRelabel (Alg. 2) on the worklist
+        for (int i = gwarp; i < nw; i += nwarps) push_relabel_warp(G, lcg(&G.wl[i]), J.kc, K);
+        if (gtid == 0) C->qcnt[0] = 0;
+        if (!grid_sync(C)) return;
+
+        // RemoveInvalidEdges (Alg. 3) on the worklist
+        for (int i = gwarp; i < nw; i += nwarps) remove_invalid_warp(G, lcg(&G.wl[i]), K);
+        if (!grid_sync(C)) return;
+    }
+
+    // ---- result and statistics -------------------------------------------
+    if (gtid == 0) {
+        C->flow = lcg(&G.e[t]) + lcg(&C->dacc[it & 1]);
+        C->iters = it;
+        for (int i = 0; i < 3; ++i) C->qcnt[i] = C->ccnt[i] = 0;
+        C->wcnt = 0;
+        C->dacc[0] = C->dacc[1] = 0;
+        C->batch_err = 0;
+    }
+    long long vals[9] = {K.bfs_verts, K.bfs_arcs, K.pr_arcs, K.push, K.relabel, K.ri_arcs, K.ri_moves, K.clamped, K.resat};
+    const int idx[9] = {S_BFS_VERTS, S_BFS_ARCS, S_PR_ARCS, S_PUSH, S_RELABEL, S_RI_ARCS, S_RI_MOVES, S_CLAMPED, S_RESAT};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const long long v = warp_sum(vals[i]);
+        if (lane == 0 && v) add_ll(&C->st[idx[i]], v);
+    }
+}
+
+__global__ void k_cut_side(const int *h, int n, unsigned char *side) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+        side[v] = h[v] >= n ? 1 : 0;
+}
+
+}  // namespace mf
+
+// =============================================================== C ABI ====
+using namespace mf;
+
+struct mf_graph {
+    int dev = 0;
+    int32_t n = 0, s = 0, t = 0;
+    int64_t m = 0, A = 0;
+    int32_t cap_limit = 0;
+    int kc = 1;
+    long long max_iters = 0;
+    int grid = 0, sms = 0;
+    mf_options opt{};
+    DevGraph dg{};
+    std::vector<void *> owned;
+    int *b_ids = nullptr, *b_caps = nullptr, *b_newc = nullptr, *b_dlt = nullptr;
+    int64_t b_cap = 0;
+    unsigned char *side_buf = nullptr;
+    unsigned seq = 0;
+    bool solved = false;
+    cudaStream_t last = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_err(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define MF_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return set_err(MF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+void *dalloc(mf_graph *g, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (g->opt.alloc) {
+        p = g->opt.alloc(bytes, g->opt.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dfree(mf_graph *g, void *p) {
+    if (!p) return;
+    if (g->opt.free) g->opt.free(p, g->opt.alloc_ctx);
+    else cudaFree(p);
+}
+
+template <class T>
+T *dnew(mf_graph *g, size_t count) {
+    T *p = static_cast<T *>(dalloc(g, count * sizeof(T)));
+    if (p) g->owned.push_back(p);
+    return p;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice;
+}
+
+template <class T>
+int host_copy(const T *src, size_t count, std::vector<T> &dst, const T **out) {
+    if (is_device_ptr(src)) {
+        dst.resize(count);
+        if (count) MF_CUDA(cudaMemcpy(dst.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost));
+        *out = dst.data();
+    } else {
+        *out = src;
+    }
+    return MF_OK;
+}
+
+int read_ctl(mf_graph *g, Ctl *out, size_t bytes = sizeof(Ctl)) {
+    MF_CUDA(cudaSetDevice(g->dev));
+    MF_CUDA(cudaMemcpyAsync(out, g->dg.ctl, bytes, cudaMemcpyDeviceToHost, g->last));
+    MF_CUDA(cudaStreamSynchronize(g->last));
+    return MF_OK;
+}
+
+int launch(mf_graph *g, const Job &job, cudaStream_t st) {
+    DevGraph dg = g->dg;
+    Job jb = job;
+    void *args[] = {&dg, &jb};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_solve, dim3(g->grid), dim3(kBlock), args, 0, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(MF_ECUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
+    }
+    g->last = st;
+    return MF_OK;
+}
+
+int ensure_batch_capacity(mf_graph *g, int64_t k, cudaStream_t st) {
+    if (k <= g->b_cap) return MF_OK;
+    int64_t want = std::max<int64_t>(k, std::max<int64_t>(1024, g->b_cap * 2));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (g->last && g->last != st) MF_CUDA(cudaStreamSynchronize(g->last));
+    int *ptrs[4] = {g->b_ids, g->b_caps, g->b_newc, g->b_dlt};
+    for (int *p : ptrs) {
+        if (!p) continue;
+        dfree(g, p);
+        g->owned.erase(std::remove(g->owned.begin(), g->owned.end(), (void *)p), g->owned.end());
+    }
+    g->b_ids = dnew<int>(g, size_t(want));
+    g->b_caps = dnew<int>(g, size_t(want));
+    g->b_newc = dnew<int>(g, size_t(want));
+    g->b_dlt = dnew<int>(g, size_t(want));
+    if (!g->b_ids || !g->b_caps || !g->b_newc || !g->b_dlt) {
+        g->b_cap = 0;
+        return set_err(MF_ENOMEM, "batch staging allocation failed");
+    }
+    g->b_cap = want;
+    return MF_OK;
+}
+
+int status_to_code(mf_graph *g, const Ctl &c) {
+    if (c.status & ST_STICKY) {
+        g->solved = false;
+        return set_err(MF_ETIMEOUT, (c.status & ST_WAIT) ? "device wait reached its time limit"
+                                                         : "device loop reached max_iters");
+    }
+    if (c.status & ST_EINVAL) {
+        int zero = c.status & ~ST_EINVAL;
+        MF_CUDA(cudaMemcpyAsync(&g->dg.ctl->status, &zero, sizeof(int), cudaMemcpyHostToDevice, g->last));
+        MF_CUDA(cudaStreamSynchronize(g->last));
+        return set_err(MF_EINVAL, "batch rejected on the device (edge id out of range, duplicate id or capacity out of range)");
+    }
+    return MF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mf_version(void) { return "0.1.0"; }
+
+const char *mf_strerror(int code) {
+    switch (code) {
+        case MF_OK: return "ok";
+        case MF_EINVAL: return "invalid argument";
+        case MF_ENOMEM: return "out of memory";
+        case MF_ECUDA: return "CUDA error";
+        case MF_ENOTSOLVED: return "graph not solved";
+        case MF_ETIMEOUT: return "device loop timeout";
+        default: return "unknown error";
+    }
+}
+
+const char *mf_last_error(void) { return g_last_error.c_str(); }
+
+int mf_options_default(mf_options *opt) {
+    if (!opt) return MF_EINVAL;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->mode = MF_MODE_DATA_DRIVEN;
+    return MF_OK;
+}
+
+int mf_bicsr_host(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, const int32_t *cap,
+                  int32_t s, int32_t t, int64_t *arcs, int64_t *arc_row, int32_t *head, int32_t *rev,
+                  int32_t *arc_cap, int32_t *arc_of_edge, int32_t *cap_limit) {
+    if (!row_ptr || (m > 0 && (!col || !cap)) || !arcs) return set_err(MF_EINVAL, "null argument");
+    HostBiCSR G;
+    int rc = build_bicsr(n, m, row_ptr, col, cap, s, t, &G);
+    if (rc) return set_err(rc == 2 ? MF_ENOMEM : MF_EINVAL, "graph rejected by the Bi-CSR builder");
+    *arcs = G.arcs;
+    if (arc_row) for (int32_t u = 0; u <= n; ++u) arc_row[u] = G.row[size_t(u)];
+    if (head) std::copy(G.head.begin(), G.head.end(), head);
+    if (rev) std::copy(G.rev.begin(), G.rev.end(), rev);
+    if (arc_cap) std::copy(G.cap.begin(), G.cap.end(), arc_cap);
+    if (arc_of_edge) std::copy(G.arc_of_edge.begin(), G.arc_of_edge.end(), arc_of_edge);
+    if (cap_limit) *cap_limit = G.cap_limit;
+    return MF_OK;
+}
+
+int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, const int32_t *cap,
+              int32_t s, int32_t t, const mf_options *opt, void *stream, mf_graph **out) {
+    if (!out || !row_ptr || (m > 0 && (!col || !cap))) return set_err(MF_EINVAL, "null argument");
+    *out = nullptr;
+    if (n < 2 || m < 0 || m >= INT32_MAX || s < 0 || t < 0 || s >= n || t >= n || s == t)
+        return set_err(MF_EINVAL, "bad sizes or terminals");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<int64_t> hrow;
+    std::vector<int32_t> hcol, hcap;
+    const int64_t *prow;
+    const int32_t *pcol = col, *pcap = cap;
+    int rc = host_copy(row_ptr, size_t(n) + 1, hrow, &prow);
+    if (rc) return rc;
+    if (m > 0) {
+        if ((rc = host_copy(col, size_t(m), hcol, &pcol))) return rc;
+        if ((rc = host_copy(cap, size_t(m), hcap, &pcap))) return rc;
+    }
+    HostBiCSR H;
+    rc = build_bicsr(n, m, prow, pcol, pcap, s, t, &H);
+    if (rc) return set_err(rc == 2 ? MF_ENOMEM : MF_EINVAL, "graph rejected by the Bi-CSR builder");
+
+    mf_graph *g = new (std::nothrow) mf_graph();
+    if (!g) return set_err(MF_ENOMEM, "host allocation");
+    if (opt) g->opt = *opt;
+    else mf_options_default(&g->opt);
+    auto fail = [&](int code, const std::string &msg) {
+        mf_destroy(g);
+        return set_err(code, msg);
+    };
+    if ((g->opt.alloc == nullptr) != (g->opt.free == nullptr)) return fail(MF_EINVAL, "alloc and free must both be set");
+    if (cudaGetDevice(&g->dev) != cudaSuccess) return fail(MF_ECUDA, "no CUDA device");
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->dev);
+    cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->dev);
+    if (!coop) return fail(MF_ECUDA, "device does not support cooperative launch");
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, kBlock, 0) != cudaSuccess || per_sm < 1)
+        return fail(MF_ECUDA, "occupancy query failed");
+    g->grid = per_sm * g->sms;
+    if (g->opt.grid_blocks > 0) g->grid = std::min(g->grid, int(g->opt.grid_blocks));
+
+    g->n = n; g->m = m; g->A = H.arcs; g->s = s; g->t = t;
+    g->cap_limit = H.cap_limit;
+    int64_t avg = (m + n / 2) / n;
+    g->kc = g->opt.kernel_cycles > 0 ? g->opt.kernel_cycles : int(std::max<int64_t>(1, avg));
+    g->max_iters = g->opt.max_iters > 0 ? g->opt.max_iters : 4LL * n + 1000;
+
+    const size_t A = size_t(std::max<int64_t>(H.arcs, 1)), N = size_t(n), M = size_t(std::max<int64_t>(m, 1));
+    DevGraph &D = g->dg;
+    D.n = n; D.s = s; D.t = t; D.m = int(m); D.A = H.arcs; D.cap_limit = H.cap_limit;
+    int *row = dnew<int>(g, N + 1), *head = dnew<int>(g, A), *rev = dnew<int>(g, A), *aoe = dnew<int>(g, M);
+    D.row = row; D.head = head; D.rev = rev; D.arc_of_edge = aoe;
+    D.cap = dnew<int>(g, A); D.r = dnew<int>(g, A); D.rr = dnew<int>(g, A);
+    D.h = dnew<int>(g, N); D.e = dnew<long long>(g, N);
+    D.cap_edge = dnew<int>(g, M); D.stamp = dnew<unsigned>(g, M);
+    D.qb0 = dnew<int>(g, N); D.qb1 = dnew<int>(g, N); D.wl = dnew<int>(g, N);
+    D.cb = dnew<int2>(g, size_t(std::max<int64_t>(H.chunk_items, 1)));
+    D.ctl = dnew<Ctl>(g, 1);
+    g->side_buf = dnew<unsigned char>(g, N);
+    if (!row || !head || !rev || !aoe || !D.cap || !D.r || !D.rr || !D.h || !D.e || !D.cap_edge || !D.stamp ||
+        !D.qb0 || !D.qb1 || !D.wl || !D.cb || !D.ctl || !g->side_buf)
+        return fail(MF_ENOMEM, "device allocation failed");
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+    };
+    std::vector<int32_t> cap_edge(pcap, pcap + m);
+    if (up(row, H.row.data(), (N + 1) * 4) || up(head, H.head.data(), size_t(H.arcs) * 4) ||
+        up(rev, H.rev.data(), size_t(H.arcs) * 4) || up(aoe, H.arc_of_edge.data(), size_t(m) * 4) ||
+        up(D.cap, H.cap.data(), size_t(H.arcs) * 4) || up(D.cap_edge, cap_edge.data(), size_t(m) * 4) ||
+        cudaMemsetAsync(D.stamp, 0, M * 4, st) || cudaMemsetAsync(D.ctl, 0, sizeof(Ctl), st) ||
+        cudaMemsetAsync(D.e, 0, N * 8, st) || cudaMemsetAsync(D.h, 0, N * 4, st) ||
+        cudaMemsetAsync(D.r, 0, A * 4, st) || cudaMemsetAsync(D.rr, 0, A * 4, st) ||
+        cudaStreamSynchronize(st)) {
+        cudaGetLastError();
+        return fail(MF_ECUDA, "upload failed");
+    }
+    g->last = st;
+    *out = g;
+    return MF_OK;
+}
+
+int mf_cap_limit(const mf_graph *g, int32_t *out) {
+    if (!g || !out) return MF_EINVAL;
+    *out = g->cap_limit;
+    return MF_OK;
+}
+
+int mf_sizes(const mf_graph *g, int32_t *n, int64_t *m, int64_t *arcs) {
+    if (!g) return MF_EINVAL;
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    if (arcs) *arcs = g->A;
+    return MF_OK;
+}
+
+int mf_solve(mf_graph *g, void *stream) {
+    if (!g) return MF_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MF_CUDA(cudaSetDevice(g->dev));
+    MF_CUDA(cudaMemsetAsync(g->dg.ctl, 0, sizeof(Ctl), st));
+    Job j{};
+    j.kind = JOB_SOLVE;
+    j.kc = g->kc;
+    j.max_iters = g->max_iters;
+    int rc = launch(g, j, st);
+    if (rc == MF_OK) g->solved = true;
+    return rc;
+}
+
+int mf_apply_updates(mf_graph *g, int64_t k, const int32_t *edge_id, const int32_t *new_cap, int32_t flags,
+                     void *stream) {
+    if (!g) return MF_EINVAL;
+    if (!g->solved) return set_err(MF_ENOTSOLVED, "call mf_solve first");
+    if (k < 0 || k > g->m || (k > 0 && (!edge_id || !new_cap)))
+        return set_err(MF_EINVAL, "bad batch size or null batch pointer");
+    if (flags & ~(MF_DEVICE_PTRS | MF_DELTA | MF_RECOMPUTE)) return set_err(MF_EINVAL, "unknown flags");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MF_CUDA(cudaSetDevice(g->dev));
+    int rc = ensure_batch_capacity(g, std::max<int64_t>(k, 1), st);
+    if (rc) return rc;
+    const int *ids = edge_id, *caps = new_cap;
+    if (!(flags & MF_DEVICE_PTRS) && k > 0) {
+        MF_CUDA(cudaMemcpyAsync(g->b_ids, edge_id, size_t(k) * 4, cudaMemcpyHostToDevice, st));
+        MF_CUDA(cudaMemcpyAsync(g->b_caps, new_cap, size_t(k) * 4, cudaMemcpyHostToDevice, st));
+        ids = g->b_ids;
+        caps = g->b_caps;
+    }
+    Job j{};
+    j.kind = (flags & MF_RECOMPUTE) ? JOB_RECOMPUTE : JOB_REPAIR;
+    j.k = int(k);
+    j.flags = flags;
+    j.kc = g->kc;
+    j.seq = ++g->seq;
+    if (g->seq == 0) j.seq = g->seq = 1;
+    j.max_iters = g->max_iters;
+    j.ids = ids;
+    j.caps = caps;
+    j.newc = g->b_newc;
+    j.dlt = g->b_dlt;
+    return launch(g, j, st);
+}
+
+int mf_sync(mf_graph *g) {
+    if (!g) return MF_EINVAL;
+    Ctl c;
+    int rc = read_ctl(g, &c);
+    if (rc) return rc;
+    return status_to_code(g, c);
+}
+
+int mf_flow_value(mf_graph *g, int64_t *out) {
+    if (!g || !out) return MF_EINVAL;
+    Ctl c;
+    int rc = read_ctl(g, &c, 16);   // status, batch_err, flow
+    if (rc) return rc;
+    rc = status_to_code(g, c);
+    if (rc == MF_ETIMEOUT) return rc;
+    if (!g->solved) return set_err(MF_ENOTSOLVED, "call mf_solve first");
+    *out = c.flow;
+    return rc;
+}
+
+int mf_min_cut(mf_graph *g, uint8_t *side, int32_t flags) {
+    if (!g || !side) return MF_EINVAL;
+    if (!g->solved) return set_err(MF_ENOTSOLVED, "call mf_solve first");
+    MF_CUDA(cudaSetDevice(g->dev));
+    unsigned char *dst = (flags & MF_DEVICE_PTRS) ? side : g->side_buf;
+    int blocks = std::max(1, std::min(g->sms * 4, (g->n + 255) / 256));
+    k_cut_side<<<blocks, 256, 0, g->last>>>(g->dg.h, g->n, dst);
+    MF_CUDA(cudaGetLastError());
+    if (!(flags & MF_DEVICE_PTRS))
+        MF_CUDA(cudaMemcpyAsync(side, g->side_buf, size_t(g->n), cudaMemcpyDeviceToHost, g->last));
+    MF_CUDA(cudaStreamSynchronize(g->last));
+    return MF_OK;
+}
+
+int mf_stats_get(mf_graph *g, mf_stats *out) {
+    if (!g || !out) return MF_EINVAL;
+    Ctl c;
+    int rc = read_ctl(g, &c);
+    if (rc) return rc;
+    std::memset(out, 0, sizeof(*out));
+    out->flow = c.flow;
+    out->iterations = c.iters;
+    out->bfs_levels = c.st[S_LEVELS];
+    out->bfs_vertices = c.st[S_BFS_VERTS];
+    out->bfs_arcs = c.st[S_BFS_ARCS];
+    out->worklist = c.st[S_WL];
+    out->pr_arcs = c.st[S_PR_ARCS];
+    out->pushes = c.st[S_PUSH];
+    out->relabels = c.st[S_RELABEL];
+    out->ri_arcs = c.st[S_RI_ARCS];
+    out->ri_moves = c.st[S_RI_MOVES];
+    out->batch = c.st[S_BATCH];
+    out->clamped = c.st[S_CLAMPED];
+    out->resat_arcs = c.st[S_RESAT];
+    out->n = g->n;
+    out->m = g->m;
+    out->arcs = g->A;
+    out->status = c.status;
+    out->kernel_cycles = g->kc;
+    out->grid_blocks = g->grid;
+    out->block_threads = kBlock;
+    return MF_OK;
+}
+
+int mf_export_graph(mf_graph *g, int64_t *arc_row, int32_t *head, int32_t *rev, int32_t *cap) {
+    if (!g) return MF_EINVAL;
+    MF_CUDA(cudaSetDevice(g->dev));
+    MF_CUDA(cudaStreamSynchronize(g->last));
+    if (arc_row) {
+        std::vector<int32_t> row(size_t(g->n) + 1);
+        MF_CUDA(cudaMemcpy(row.data(), g->dg.row, row.size() * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < row.size(); ++i) arc_row[i] = row[i];
+    }
+    if (head && g->A) MF_CUDA(cudaMemcpy(head, g->dg.head, size_t(g->A) * 4, cudaMemcpyDeviceToHost));
+    if (rev && g->A) MF_CUDA(cudaMemcpy(rev, g->dg.rev, size_t(g->A) * 4, cudaMemcpyDeviceToHost));
+    if (cap && g->A) MF_CUDA(cudaMemcpy(cap, g->dg.cap, size_t(g->A) * 4, cudaMemcpyDeviceToHost));
+    return MF_OK;
+}
+
+int mf_export_state(mf_graph *g, int32_t *r, int64_t *excess, int32_t *height, int32_t flags) {
+    if (!g) return MF_EINVAL;
+    MF_CUDA(cudaSetDevice(g->dev));
+    cudaMemcpyKind kind = (flags & MF_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (r && g->A) MF_CUDA(cudaMemcpyAsync(r, g->dg.r, size_t(g->A) * 4, kind, g->last));
+    if (excess) MF_CUDA(cudaMemcpyAsync(excess, g->dg.e, size_t(g->n) * 8, kind, g->last));
+    if (height) MF_CUDA(cudaMemcpyAsync(height, g->dg.h, size_t(g->n) * 4, kind, g->last));
+    MF_CUDA(cudaStreamSynchronize(g->last));
+    return MF_OK;
+}
+
+int mf_import_state(mf_graph *g, const int32_t *r, const int64_t *excess, const int32_t *height, int32_t flags) {
+    if (!g || !r || !excess || !height) return MF_EINVAL;
+    MF_CUDA(cudaSetDevice(g->dev));
+    cudaMemcpyKind kind = (flags & MF_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    MF_CUDA(cudaStreamSynchronize(g->last));
+    if (g->A) MF_CUDA(cudaMemcpy(g->dg.r, r, size_t(g->A) * 4, kind));
+    MF_CUDA(cudaMemcpy(g->dg.e, excess, size_t(g->n) * 8, kind));
+    MF_CUDA(cudaMemcpy(g->dg.h, height, size_t(g->n) * 4, kind));
+    // rebuild the mirror rr[a] = r[rev[a]] on the host side of the copy
+    std::vector<int32_t> hr(size_t(g->A)), hrev(size_t(g->A)), hrr(size_t(g->A));
+    if (g->A) {
+        MF_CUDA(cudaMemcpy(hr.data(), g->dg.r, size_t(g->A) * 4, cudaMemcpyDeviceToHost));
+        MF_CUDA(cudaMemcpy(hrev.data(), g->dg.rev, size_t(g->A) * 4, cudaMemcpyDeviceToHost));
+        for (size_t a = 0; a < hr.size(); ++a) hrr[a] = hr[size_t(hrev[a])];
+        MF_CUDA(cudaMemcpy(g->dg.rr, hrr.data(), size_t(g->A) * 4, cudaMemcpyHostToDevice));
+    }
+    // value of the imported state: e(t) plus the deficits (Alg. 4, final sum)
+    std::vector<int64_t> he(size_t(g->n));
+    MF_CUDA(cudaMemcpy(he.data(), g->dg.e, size_t(g->n) * 8, cudaMemcpyDeviceToHost));
+    long long flow = he[size_t(g->t)];
+    for (int32_t v = 0; v < g->n; ++v)
+        if (v != g->s && v != g->t && he[size_t(v)] < 0) flow += he[size_t(v)];
+    MF_CUDA(cudaMemset(g->dg.ctl, 0, sizeof(Ctl)));
+    MF_CUDA(cudaMemcpy(&g->dg.ctl->flow, &flow, sizeof(flow), cudaMemcpyHostToDevice));
+    MF_CUDA(cudaDeviceSynchronize());
+    g->solved = true;
+    return MF_OK;
+}
+
+void mf_destroy(mf_graph *g) {
+    if (!g) return;
+    cudaSetDevice(g->dev);
+    if (g->last) cudaStreamSynchronize(g->last);
+    cudaDeviceSynchronize();
+    for (void *p : g->owned) dfree(g, p);
+    delete g;
+}
+
+}  // extern "C"
