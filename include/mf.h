@@ -67,6 +67,9 @@ typedef struct mf_graph mf_graph;
  *  grid_blocks    CTAs of the persistent solver kernel; 0 = one full wave
  *                 (co-resident CTAs per SM x SM count).  Larger values are
  *                 clamped to one full wave.
+ *  time_limit_ms  wall-clock limit of one solve/repair kernel, checked once
+ *                 per loop iteration; passing it reports MF_ETIMEOUT.
+ *                 0 = 60000.
  *  alloc / free   device allocator callbacks (both NULL = cudaMalloc/cudaFree).
  *                 alloc(bytes, ctx) returns a device pointer or NULL. */
 typedef struct mf_options {
@@ -74,7 +77,7 @@ typedef struct mf_options {
     int32_t mode;
     int64_t max_iters;
     int32_t grid_blocks;
-    int32_t reserved0;
+    int32_t time_limit_ms;
     void *(*alloc)(size_t bytes, void *ctx);
     void (*free)(void *ptr, void *ctx);
     void *alloc_ctx;

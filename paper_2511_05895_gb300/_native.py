@@ -26,7 +26,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 class Options(ctypes.Structure):
     _fields_ = [("kernel_cycles", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("max_iters", ctypes.c_int64), ("grid_blocks", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("time_limit_ms", ctypes.c_int32), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", ctypes.c_void_p)]
 
 
@@ -171,13 +171,14 @@ class MaxFlowGraph:
     (CPU or CUDA); the stream defaults to torch's current stream."""
 
     def __init__(self, n, row_ptr, col, cap, s, t, *, kernel_cycles=0, max_iters=0,
-                 grid_blocks=0, torch_allocator=False, stream=None):
+                 grid_blocks=0, time_limit_ms=0, torch_allocator=False, stream=None):
         L = lib()
         self._opt = Options()
         L.mf_options_default(ctypes.byref(self._opt))
         self._opt.kernel_cycles = kernel_cycles
         self._opt.max_iters = max_iters
         self._opt.grid_blocks = grid_blocks
+        self._opt.time_limit_ms = time_limit_ms
         self._keep = []
         if torch_allocator:
             torch = _torch()

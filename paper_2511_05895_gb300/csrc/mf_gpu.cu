@@ -46,7 +46,8 @@ constexpr unsigned long long kWaitNs = 20ull * 1000ull * 1000ull * 1000ull;  // 
 constexpr int ST_EINVAL = 1;   // rejected batch (state unchanged)
 constexpr int ST_ITERS = 2;    // max_iters reached
 constexpr int ST_WAIT = 4;     // a grid-barrier wait reached its time limit
-constexpr int ST_STICKY = ST_ITERS | ST_WAIT;
+constexpr int ST_TIME = 8;     // the kernel ran past its wall-clock limit
+constexpr int ST_STICKY = ST_ITERS | ST_WAIT | ST_TIME;
 
 enum JobKind { JOB_SOLVE = 0, JOB_REPAIR = 1, JOB_RECOMPUTE = 2 };
 
@@ -65,6 +66,9 @@ struct Ctl {
     int pad0;
     long long dacc[2];    // (z) sum of deficits at the last height init
     long long iters;
+    unsigned long long t_start;  // globaltimer at kernel entry
+    int abort_loop;       // (z) set by thread 0 when the wall-clock limit passed
+    int pad1;
     long long st[12];     // statistics, see enum Stat
 };
 
@@ -90,6 +94,7 @@ struct Job {
     int kind, k, flags, kc;
     unsigned seq;
     long long max_iters;
+    unsigned long long time_limit_ns;
     const int *ids, *caps;
     int *newc, *dlt;
 };
@@ -336,6 +341,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
     if (gtid == 0) {
         for (int i = 0; i < S_COUNT; ++i) C->st[i] = 0;
         C->st[S_BATCH] = J.kind == JOB_SOLVE ? 0 : J.k;
+        C->t_start = gtimer();
     }
 
     // ---- batch: validate, then apply (Algorithm 5) ----------------------
@@ -451,6 +457,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             C->ccnt[0] = 0;
             C->wcnt = 0;
             C->dacc[par ^ 1] = 0;
+            if (gtimer() - C->t_start > J.time_limit_ns) C->abort_loop = 1;
         }
         {
             long long dsum = 0;
@@ -520,6 +527,10 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             if (gtid == 0) atomicOr(&C->status, ST_ITERS);
             break;
         }
+        if (lcg(&C->abort_loop)) {   // written before the height-init barrier
+            if (gtid == 0) atomicOr(&C->status, ST_TIME);
+            break;
+        }
         if (gtid == 0) C->st[S_WL] += nw;
 
         // PushRelabel (Alg. 2) on the worklist
@@ -540,6 +551,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
         C->wcnt = 0;
         C->dacc[0] = C->dacc[1] = 0;
         C->batch_err = 0;
+        C->abort_loop = 0;
     }
     long long vals[9] = {K.bfs_verts, K.bfs_arcs, K.pr_arcs, K.push, K.relabel, K.ri_arcs, K.ri_moves, K.clamped, K.resat};
     const int idx[9] = {S_BFS_VERTS, S_BFS_ARCS, S_PR_ARCS, S_PUSH, S_RELABEL, S_RI_ARCS, S_RI_MOVES, S_CLAMPED, S_RESAT};
@@ -567,6 +579,7 @@ struct mf_graph {
     int32_t cap_limit = 0;
     int kc = 1;
     long long max_iters = 0;
+    unsigned long long time_limit_ns = 0;
     int grid = 0, sms = 0;
     mf_options opt{};
     DevGraph dg{};
@@ -687,8 +700,9 @@ int ensure_batch_capacity(mf_graph *g, int64_t k, cudaStream_t st) {
 int status_to_code(mf_graph *g, const Ctl &c) {
     if (c.status & ST_STICKY) {
         g->solved = false;
-        return set_err(MF_ETIMEOUT, (c.status & ST_WAIT) ? "device wait reached its time limit"
-                                                         : "device loop reached max_iters");
+        return set_err(MF_ETIMEOUT, (c.status & ST_WAIT)   ? "device wait reached its time limit"
+                                    : (c.status & ST_TIME) ? "device loop reached its wall-clock limit"
+                                                           : "device loop reached max_iters");
     }
     if (c.status & ST_EINVAL) {
         int zero = c.status & ~ST_EINVAL;
@@ -789,6 +803,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     int64_t avg = (m + n / 2) / n;
     g->kc = g->opt.kernel_cycles > 0 ? g->opt.kernel_cycles : int(std::max<int64_t>(1, avg));
     g->max_iters = g->opt.max_iters > 0 ? g->opt.max_iters : 4LL * n + 1000;
+    g->time_limit_ns = 1000000ull * (unsigned long long)(g->opt.time_limit_ms > 0 ? g->opt.time_limit_ms : 60000);
 
     const size_t A = size_t(std::max<int64_t>(H.arcs, 1)), N = size_t(n), M = size_t(std::max<int64_t>(m, 1));
     DevGraph &D = g->dg;
@@ -847,6 +862,7 @@ int mf_solve(mf_graph *g, void *stream) {
     j.kind = JOB_SOLVE;
     j.kc = g->kc;
     j.max_iters = g->max_iters;
+    j.time_limit_ns = g->time_limit_ns;
     int rc = launch(g, j, st);
     if (rc == MF_OK) g->solved = true;
     return rc;
@@ -878,6 +894,7 @@ int mf_apply_updates(mf_graph *g, int64_t k, const int32_t *edge_id, const int32
     j.seq = ++g->seq;
     if (g->seq == 0) j.seq = g->seq = 1;
     j.max_iters = g->max_iters;
+    j.time_limit_ns = g->time_limit_ns;
     j.ids = ids;
     j.caps = caps;
     j.newc = g->b_newc;
