@@ -249,7 +249,7 @@ def main():
     for i in range(args.warmup):
         timed_step(*dev[i])
     G.sync()
-    stats_acc = {k: 0 for k in list(BYTES) + ["iterations"]}
+    stats_acc = {k: 0 for k in [b for b in BYTES if b != "height_init"] + ["iterations", "bfs_levels"]}
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()
