@@ -249,7 +249,9 @@ def main():
     for i in range(args.warmup):
         timed_step(*dev[i])
     G.sync()
-    stats_acc = {k: 0 for k in [b for b in BYTES if b != "height_init"] + ["iterations", "bfs_levels"]}
+    stats_acc = {k: 0 for k in [b for b in BYTES if b != "height_init"] +
+                 ["iterations", "bfs_levels", "t_batch_ns", "t_reset_ns", "t_bfs_ns", "t_pr_ns",
+                  "t_hub_ns", "t_ri_ns", "hub_cycles", "barriers"]}
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()

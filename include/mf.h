@@ -94,7 +94,12 @@ typedef struct mf_options {
  *  ri_arcs, ri_moves  arcs scanned / saturated by RemoveInvalidEdges (Alg. 3)
  *  batch        entries of the last batch (0 for mf_solve)
  *  clamped      arcs whose residual went negative and was clamped (Alg. 5)
- *  resat_arcs   source arcs scanned by the re-saturation step (Alg. 4) */
+ *  resat_arcs   source arcs scanned by the re-saturation step (Alg. 4)
+ *  t_*_ns       device time per phase (globaltimer between grid barriers):
+ *               batch + re-saturation, height init, BFS, warp PushRelabel,
+ *               hub PushRelabel cycles, RemoveInvalidEdges
+ *  hub_cycles   cooperative PushRelabel cycles of high-degree vertices
+ *  barriers     grid barriers passed */
 typedef struct mf_stats {
     int64_t flow;
     int64_t iterations;
@@ -113,6 +118,14 @@ typedef struct mf_stats {
     int64_t n;
     int64_t m;
     int64_t arcs;
+    int64_t t_batch_ns;
+    int64_t t_reset_ns;
+    int64_t t_bfs_ns;
+    int64_t t_pr_ns;
+    int64_t t_hub_ns;
+    int64_t t_ri_ns;
+    int64_t hub_cycles;
+    int64_t barriers;
     int32_t status;
     int32_t kernel_cycles;
     int32_t grid_blocks;

@@ -144,11 +144,17 @@ int build_bicsr(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col
             if (cap[i] > G.cap_limit) return 1;
         // 5. work-item bound for big vertices
         G.chunk_items = 0;
+        G.hubs = 0;
+        G.hub_chunk_items = 0;
         G.max_deg = 0;
         for (int32_t u = 0; u < n; ++u) {
             int32_t d = G.row[size_t(u) + 1] - G.row[size_t(u)];
             G.max_deg = std::max(G.max_deg, d);
             if (d > kBigDeg) G.chunk_items += (d + kChunk - 1) / kChunk;
+            if (d > kHubDeg) {
+                G.hubs += 1;
+                G.hub_chunk_items += (d + kPrChunk - 1) / kPrChunk;
+            }
         }
     } catch (const std::bad_alloc &) {
         return 2;

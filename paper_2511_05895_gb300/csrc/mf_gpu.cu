@@ -51,6 +51,8 @@ constexpr int ST_STICKY = ST_ITERS | ST_WAIT | ST_TIME;
 
 enum JobKind { JOB_SOLVE = 0, JOB_REPAIR = 1, JOB_RECOMPUTE = 2 };
 
+constexpr int S_COUNT_MAX = 24;
+
 // Device control block.  Fields marked (z) are zero whenever no k_solve is
 // running: they are zeroed at creation, by mf_solve, and by the last thread
 // of every k_solve that ends normally.
@@ -62,20 +64,27 @@ struct Ctl {
     unsigned bar_gen;     // grid barrier generation
     int qcnt[3];          // (z) BFS frontier sizes, rotating by level
     int ccnt[3];          // (z) BFS chunk-item counts, rotating by level
-    int wcnt;             // (z) active worklist size
+    int wcnt;             // (z) active worklist size (vertices of degree <= kHubDeg)
+    int hcnt;             // (z) active hub list size (degree > kHubDeg)
+    int hccnt;            // (z) hub work items
+    int hub_act[2];       // (z) hubs still active in the current hub cycle
     int pad0;
     long long dacc[2];    // (z) sum of deficits at the last height init
     long long iters;
     unsigned long long t_start;  // globaltimer at kernel entry
     int abort_loop;       // (z) set by thread 0 when the wall-clock limit passed
     int pad1;
-    long long st[12];     // statistics, see enum Stat
+    long long st[S_COUNT_MAX];  // statistics, see enum Stat
 };
 
 enum Stat {
     S_LEVELS, S_BFS_VERTS, S_BFS_ARCS, S_WL, S_PR_ARCS, S_PUSH, S_RELABEL, S_RI_ARCS, S_RI_MOVES,
-    S_BATCH, S_CLAMPED, S_RESAT, S_COUNT
+    S_BATCH, S_CLAMPED, S_RESAT,
+    // phase times (ns, globaltimer of CTA 0 between grid barriers) and counts
+    S_T_BATCH, S_T_RESET, S_T_BFS, S_T_PRW, S_T_HUB, S_T_RI, S_HUB_CYCLES, S_BARRIERS,
+    S_COUNT
 };
+static_assert(S_COUNT <= S_COUNT_MAX, "statistics array too small");
 
 struct DevGraph {
     int n, s, t, m;
@@ -87,6 +96,10 @@ struct DevGraph {
     unsigned *stamp;
     int *qb0, *qb1, *wl;
     int2 *cb;
+    int *hl, *hmode;          // active hubs; per-hub cycle state
+    int2 *hcl;                // hub work items (hub index, first arc)
+    unsigned long long *hkey; // per-hub lowest (height, arc) key
+    long long *hrem;          // per-hub excess left to push in the current cycle
     Ctl *ctl;
 };
 
@@ -133,6 +146,16 @@ __device__ __forceinline__ unsigned long long warp_min(unsigned long long v) {
         v = w < v ? w : v;
     }
     return v;
+}
+
+__device__ __forceinline__ long long warp_incl_scan(long long x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
 }
 
 // Warp-aggregated append: one atomicAdd per warp (Sec. 5.3: ballot, then the
@@ -203,7 +226,12 @@ __device__ __forceinline__ void bfs_visit(const DevGraph &G, bool valid, int a, 
     }
     warp_append(disc, v, ncnt, NF);
     const bool act = disc && lcg(&G.e[v]) > 0;
-    warp_append(act, v, &G.ctl->wcnt, G.wl);
+    if (__ballot_sync(kFull, act)) {
+        bool hub = false;
+        if (act) hub = __ldg(&G.row[v + 1]) - __ldg(&G.row[v]) > kHubDeg;
+        warp_append(act && !hub, v, &G.ctl->wcnt, G.wl);
+        warp_append(hub, v, &G.ctl->hcnt, G.hl);
+    }
     if (disc) ++K.bfs_verts;
 }
 
@@ -237,16 +265,30 @@ __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int 
 }
 
 // ------------------------------------------------------ push / relabel --
-// Algorithm 2 on vertex u by one warp: up to kc times, find the lowest
-// residual neighbour (ties: lowest arc), then push min(e, c_f) to it with
-// atomics, or relabel u to one above it.  Neighbour heights are read once per
-// step (Note 3 of Sec. 3).  A vertex without residual arcs gets height n.
+// One push of d units along arc a (u -> v): both residual copies of the arc
+// pair and the head's excess; the caller subtracts the total from e(u).
+__device__ __forceinline__ void push_arc(const DevGraph &G, int a, int v, int d) {
+    const int b = __ldg(&G.rev[a]);
+    atomicSub(&G.r[a], d);
+    atomicSub(&G.rr[b], d);
+    atomicAdd(&G.r[b], d);
+    atomicAdd(&G.rr[a], d);
+    add_ll(&G.e[v], (long long)d);
+}
+
+// Algorithm 2 on vertex u by one warp, up to kc cycles.  A cycle scans u's
+// arcs once for the lowest residual neighbour height h^ (ties: lowest arc;
+// heights read once per cycle, Note 3 of Sec. 3).  If h(u) > h^ the cycle
+// performs the pushes that consecutive Alg. 2 steps would make to the arcs at
+// height h^ -- in arc order, min(e, c_f) each, until e(u) is used up -- with a
+// second pass over the arcs; otherwise it relabels u to h^ + 1.  A vertex
+// without residual arcs gets height n.  Only u's warp lowers r(u, .) and e(u);
+// other warps only raise them, so every amount pushed is available.
 __device__ void push_relabel_warp(const DevGraph &G, int u, int kc, Counters &K) {
     const int lane = threadIdx.x & 31;
     const int n = G.n;
     const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
     for (int c = 0; c < kc; ++c) {
-        // lane 0 reads h(u) and e(u) once; the warp follows its copy
         int hu = 0;
         long long eu = 0;
         if (lane == 0) {
@@ -267,34 +309,47 @@ __device__ void push_relabel_warp(const DevGraph &G, int u, int kc, Counters &K)
             }
         }
         best = warp_min(best);
-        if (lane == 0) {
-            if (best == ~0ull) {
+        if (best == ~0ull) {
+            if (lane == 0) {
                 G.h[u] = n;
                 ++K.relabel;
-            } else {
-                const int hh = (int)(best >> 32);
-                const int a = beg + (int)(best & 0xffffffffu);
-                if (hu > hh) {
-                    const int ra = lcg(&G.r[a]);
-                    const long long d = eu < (long long)ra ? eu : (long long)ra;
-                    if (d > 0) {
-                        const int v = __ldg(&G.head[a]);
-                        const int b = __ldg(&G.rev[a]);
-                        const int di = (int)d;
-                        atomicSub(&G.r[a], di);
-                        atomicSub(&G.rr[b], di);
-                        atomicAdd(&G.r[b], di);
-                        atomicAdd(&G.rr[a], di);
-                        add_ll(&G.e[u], -d);
-                        add_ll(&G.e[v], d);
-                        ++K.push;
-                    }
-                } else {
-                    G.h[u] = hh + 1;
-                    ++K.relabel;
+            }
+            break;
+        }
+        const int hh = (int)(best >> 32);
+        if (hu <= hh) {
+            if (lane == 0) {
+                G.h[u] = hh + 1;
+                ++K.relabel;
+            }
+            __syncwarp();
+            continue;
+        }
+        long long rem = eu, sent = 0;
+        for (int base = beg; base < end && rem > 0; base += 32) {
+            const int a = base + lane;
+            int ra = 0, v = 0;
+            if (a < end) {
+                ++K.pr_arcs;
+                ra = lcg(&G.r[a]);
+                if (ra > 0) {
+                    v = __ldg(&G.head[a]);
+                    if (lcg(&G.h[v]) != hh) ra = 0;
                 }
             }
+            const long long incl = warp_incl_scan(ra);
+            long long d = rem - (incl - ra);
+            d = d < 0 ? 0 : (d > ra ? ra : d);
+            if (d > 0) {
+                push_arc(G, a, v, (int)d);
+                sent += d;
+                ++K.push;
+            }
+            const long long tot = __shfl_sync(kFull, incl, 31);
+            rem -= tot < rem ? tot : rem;
         }
+        sent = warp_sum(sent);
+        if (lane == 0 && sent) add_ll(&G.e[u], -sent);
         __syncwarp();
     }
 }
@@ -311,13 +366,8 @@ __device__ void remove_invalid_warp(const DevGraph &G, int u, Counters &K) {
         if (ra > 0) {
             const int v = __ldg(&G.head[a]);
             if (hu > lcg(&G.h[v]) + 1) {
-                const int b = __ldg(&G.rev[a]);
-                atomicSub(&G.r[a], ra);
-                atomicSub(&G.rr[b], ra);
-                atomicAdd(&G.r[b], ra);
-                atomicAdd(&G.rr[a], ra);
+                push_arc(G, a, v, ra);
                 add_ll(&G.e[u], -(long long)ra);
-                add_ll(&G.e[v], (long long)ra);
                 ++K.ri_moves;
             }
         }
@@ -325,6 +375,19 @@ __device__ void remove_invalid_warp(const DevGraph &G, int u, Counters &K) {
 }
 
 // ------------------------------------------------------------ the kernel --
+// Grid barrier inside k_solve; CTA 0's thread 0 charges the time since the
+// previous barrier to a phase bucket of the statistics.
+#define MF_SYNC(bucket)                                                       \
+    do {                                                                      \
+        if (!grid_sync(C)) return;                                            \
+        if (gtid == 0) {                                                      \
+            const unsigned long long now_ = gtimer();                         \
+            C->st[bucket] += (long long)(now_ - tprev);                       \
+            C->st[S_BARRIERS] += 1;                                           \
+            tprev = now_;                                                     \
+        }                                                                     \
+    } while (0)
+
 __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
     Ctl *C = G.ctl;
     const int lane = threadIdx.x & 31;
@@ -334,6 +397,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
     const int nwarps = (int)(gthreads >> 5);
     const int n = G.n, s = G.s, t = G.t;
     Counters K;
+    unsigned long long tprev = gtimer();
 
     // A sticky error (iteration cap, barrier wait) invalidates the state
     // until the next mf_solve, which clears it before launching.
@@ -363,7 +427,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             J.newc[i] = nc;
             if (bad) atomicOr(&C->batch_err, 1);
         }
-        if (!grid_sync(C)) return;
+        MF_SYNC(S_T_BATCH);
         if (lcg(&C->batch_err)) {
             grid_sync(C);
             if (gtid == 0) {
@@ -388,7 +452,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
                 }
             }
         }
-        if (!grid_sync(C)) return;
+        MF_SYNC(S_T_BATCH);
         if (J.kind == JOB_REPAIR) {
             // flow above the new capacity goes back: the tail keeps it as
             // excess, the head becomes deficient (Alg. 5, lines 4-11; the
@@ -409,7 +473,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
                     ++K.clamped;
                 }
             }
-            if (!grid_sync(C)) return;
+            MF_SYNC(S_T_BATCH);
         }
     }
 
@@ -420,7 +484,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             G.rr[a] = lcg(&G.cap[__ldg(&G.rev[a])]);
         }
         for (long long v = gtid; v < n; v += gthreads) G.e[v] = 0;
-        if (!grid_sync(C)) return;
+        MF_SYNC(S_T_BATCH);
     }
 
     // ---- saturate the source arcs (Alg. 1 third loop, Alg. 4 lines 3-7) --
@@ -442,7 +506,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
         }
         moved = warp_sum(moved);
         if (lane == 0 && moved) add_ll(&G.e[s], -moved);
-        if (!grid_sync(C)) return;
+        MF_SYNC(S_T_BATCH);
     }
 
     // ---- device loop (Algorithm 4 while-loop) ----------------------------
@@ -456,6 +520,9 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             C->qcnt[2] = 0;
             C->ccnt[0] = 0;
             C->wcnt = 0;
+            C->hcnt = 0;
+            C->hccnt = 0;
+            C->hub_act[0] = C->hub_act[1] = 0;
             C->dacc[par ^ 1] = 0;
             if (gtimer() - C->t_start > J.time_limit_ns) C->abort_loop = 1;
         }
@@ -475,7 +542,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             dsum = warp_sum(dsum);
             if (lane == 0 && dsum) add_ll(&C->dacc[par], dsum);
         }
-        if (!grid_sync(C)) return;
+        MF_SYNC(S_T_RESET);
 
         // backward BFS from the sinks over residual arcs (global relabel)
         int L = 0;
@@ -506,7 +573,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
                 }
                 bfs_expand_warp(G, beg, deg, L, ncnt, NF, K);
             }
-            if (!grid_sync(C)) return;
+            MF_SYNC(S_T_BFS);
             const int nch = lcg(ccnt);
             if (nch > 0) {
                 for (int c = gwarp; c < nch; c += nwarps) {
@@ -514,7 +581,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
                     const int a1 = min(item.y + kChunk, __ldg(&G.row[item.x + 1]));
                     for (int ab = item.y; ab < a1; ab += 32) bfs_visit(G, ab + lane < a1, ab + lane, L, ncnt, NF, K);
                 }
-                if (!grid_sync(C)) return;
+                MF_SYNC(S_T_BFS);
             }
             ++L;
         }
@@ -522,7 +589,8 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
 
         // termination: no active vertex under the fresh BFS heights
         const int nw = lcg(&C->wcnt);
-        if (nw == 0) break;
+        const int nh = lcg(&C->hcnt);
+        if (nw == 0 && nh == 0) break;
         if (it >= J.max_iters) {
             if (gtid == 0) atomicOr(&C->status, ST_ITERS);
             break;
@@ -531,16 +599,155 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             if (gtid == 0) atomicOr(&C->status, ST_TIME);
             break;
         }
-        if (gtid == 0) C->st[S_WL] += nw;
+        if (gtid == 0) C->st[S_WL] += nw + nh;
 
-        // PushRelabel (Alg. 2) on the worklist
+        // PushRelabel (Alg. 2): one warp per worklist vertex ...
         for (int i = gwarp; i < nw; i += nwarps) push_relabel_warp(G, lcg(&G.wl[i]), J.kc, K);
         if (gtid == 0) C->qcnt[0] = 0;
-        if (!grid_sync(C)) return;
+        // ... and the hubs together, kPrChunk-arc items over the whole grid
+        int nhc = 0;
+        if (nh > 0) {
+            for (int i = gwarp; i < nh; i += nwarps) {
+                const int u = lcg(&G.hl[i]);
+                const int beg = __ldg(&G.row[u]);
+                const int nc = (__ldg(&G.row[u + 1]) - beg + kPrChunk - 1) / kPrChunk;
+                int pos = 0;
+                if (lane == 0) {
+                    pos = atomicAdd(&C->hccnt, nc);
+                    G.hkey[i] = ~0ull;
+                    G.hmode[i] = 0;
+                }
+                pos = __shfl_sync(kFull, pos, 0);
+                for (int c = lane; c < nc; c += 32) G.hcl[pos + c] = make_int2(i, beg + c * kPrChunk);
+            }
+            MF_SYNC(S_T_PRW);
+            nhc = lcg(&C->hccnt);
+            for (int c = 0; c < J.kc; ++c) {
+                if (gtid == 0) C->st[S_HUB_CYCLES] += 1;
+                // H1: lowest residual neighbour of every unfinished hub
+                for (int w = gwarp; w < nhc; w += nwarps) {
+                    const int2 item = lcg(&G.hcl[w]);
+                    if (lcg(&G.hmode[item.x]) < 0) continue;
+                    const int u = lcg(&G.hl[item.x]);
+                    const int beg = __ldg(&G.row[u]);
+                    const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
+                    unsigned long long best = ~0ull;
+                    for (int a = item.y + lane; a < a1; a += 32) {
+                        const int ra = lcg(&G.r[a]);
+                        ++K.pr_arcs;
+                        if (ra > 0) {
+                            const unsigned hv = (unsigned)lcg(&G.h[__ldg(&G.head[a])]);
+                            const unsigned long long key = ((unsigned long long)hv << 32) | (unsigned)(a - beg);
+                            best = key < best ? key : best;
+                        }
+                    }
+                    best = warp_min(best);
+                    if (lane == 0 && best != ~0ull) atomicMin(&G.hkey[item.x], best);
+                }
+                MF_SYNC(S_T_HUB);
+                // H2: per hub, push at the lowest height, relabel, or finish
+                for (long long i = gtid; i < nh; i += gthreads) {
+                    if (lcg(&G.hmode[i]) < 0) continue;
+                    const int u = lcg(&G.hl[i]);
+                    const int hu = lcg(&G.h[u]);
+                    const long long eu = lcg(&G.e[u]);
+                    const unsigned long long key = __ldcg(&G.hkey[i]);
+                    G.hkey[i] = ~0ull;
+                    int mode;
+                    if (hu >= n || eu <= 0) {
+                        mode = -1;
+                    } else if (key == ~0ull) {
+                        G.h[u] = n;
+                        ++K.relabel;
+                        mode = -1;
+                    } else {
+                        const int hh = (int)(key >> 32);
+                        if (hu > hh) {
+                            mode = hh + 1;          // push to the arcs at height hh
+                            G.hrem[i] = eu;
+                        } else {
+                            G.h[u] = hh + 1;
+                            ++K.relabel;
+                            mode = 0;
+                        }
+                    }
+                    G.hmode[i] = mode;
+                    if (mode >= 0) atomicAdd(&C->hub_act[c & 1], 1);
+                }
+                if (gtid == 0) C->hub_act[(c + 1) & 1] = 0;
+                MF_SYNC(S_T_HUB);
+                // H3: pushes along the lowest arcs; each warp reserves its share
+                // of the hub's excess with one atomic
+                for (int w = gwarp; w < nhc; w += nwarps) {
+                    const int2 item = lcg(&G.hcl[w]);
+                    const int mode = lcg(&G.hmode[item.x]);
+                    if (mode <= 0) continue;
+                    const int hh = mode - 1;
+                    const int u = lcg(&G.hl[item.x]);
+                    const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
+                    long long sent = 0;
+                    for (int base = item.y; base < a1; base += 32) {
+                        const int a = base + lane;
+                        int ra = 0, v = 0;
+                        if (a < a1) {
+                            ++K.pr_arcs;
+                            ra = lcg(&G.r[a]);
+                            if (ra > 0) {
+                                v = __ldg(&G.head[a]);
+                                if (lcg(&G.h[v]) != hh) ra = 0;
+                            }
+                        }
+                        const long long incl = warp_incl_scan(ra);
+                        const long long tot = __shfl_sync(kFull, incl, 31);
+                        if (tot == 0) continue;
+                        long long old = 0;
+                        if (lane == 0)
+                            old = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&G.hrem[item.x]),
+                                                       (unsigned long long)(-tot));
+                        old = __shfl_sync(kFull, old, 0);
+                        if (old <= 0) break;
+                        long long d = old - (incl - ra);
+                        d = d < 0 ? 0 : (d > ra ? ra : d);
+                        if (d > 0) {
+                            push_arc(G, a, v, (int)d);
+                            sent += d;
+                            ++K.push;
+                        }
+                    }
+                    sent = warp_sum(sent);
+                    if (lane == 0 && sent) add_ll(&G.e[u], -sent);
+                }
+                MF_SYNC(S_T_HUB);
+                if (lcg(&C->hub_act[c & 1]) == 0) break;
+            }
+        } else {
+            MF_SYNC(S_T_PRW);
+        }
 
-        // RemoveInvalidEdges (Alg. 3) on the worklist
+        // RemoveInvalidEdges (Alg. 3): worklist vertices by warps, hubs by items
         for (int i = gwarp; i < nw; i += nwarps) remove_invalid_warp(G, lcg(&G.wl[i]), K);
-        if (!grid_sync(C)) return;
+        for (int w = gwarp; w < nhc; w += nwarps) {
+            const int2 item = lcg(&G.hcl[w]);
+            const int u = lcg(&G.hl[item.x]);
+            const int hu = lcg(&G.h[u]);
+            const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
+            long long moved = 0;
+            for (int a = item.y + lane; a < a1; a += 32) {
+                const int ra = lcg(&G.r[a]);
+                ++K.ri_arcs;
+                if (ra > 0) {
+                    const int v = __ldg(&G.head[a]);
+                    if (hu > lcg(&G.h[v]) + 1) {
+                        push_arc(G, a, v, ra);
+                        moved += ra;
+                        ++K.ri_moves;
+                    }
+                }
+            }
+            moved = warp_sum(moved);
+            if (lane == 0 && moved) add_ll(&G.e[u], -moved);
+        }
+        MF_SYNC(S_T_RI);
     }
 
     // ---- result and statistics -------------------------------------------
@@ -548,7 +755,8 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
         C->flow = lcg(&G.e[t]) + lcg(&C->dacc[it & 1]);
         C->iters = it;
         for (int i = 0; i < 3; ++i) C->qcnt[i] = C->ccnt[i] = 0;
-        C->wcnt = 0;
+        C->wcnt = C->hcnt = C->hccnt = 0;
+        C->hub_act[0] = C->hub_act[1] = 0;
         C->dacc[0] = C->dacc[1] = 0;
         C->batch_err = 0;
         C->abort_loop = 0;
@@ -815,10 +1023,17 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     D.cap_edge = dnew<int>(g, M); D.stamp = dnew<unsigned>(g, M);
     D.qb0 = dnew<int>(g, N); D.qb1 = dnew<int>(g, N); D.wl = dnew<int>(g, N);
     D.cb = dnew<int2>(g, size_t(std::max<int64_t>(H.chunk_items, 1)));
+    const size_t NH = size_t(std::max<int64_t>(H.hubs, 1));
+    D.hl = dnew<int>(g, NH);
+    D.hmode = dnew<int>(g, NH);
+    D.hkey = dnew<unsigned long long>(g, NH);
+    D.hrem = dnew<long long>(g, NH);
+    D.hcl = dnew<int2>(g, size_t(std::max<int64_t>(H.hub_chunk_items, 1)));
     D.ctl = dnew<Ctl>(g, 1);
     g->side_buf = dnew<unsigned char>(g, N);
     if (!row || !head || !rev || !aoe || !D.cap || !D.r || !D.rr || !D.h || !D.e || !D.cap_edge || !D.stamp ||
-        !D.qb0 || !D.qb1 || !D.wl || !D.cb || !D.ctl || !g->side_buf)
+        !D.qb0 || !D.qb1 || !D.wl || !D.cb || !D.ctl || !g->side_buf || !D.hl || !D.hmode || !D.hkey ||
+        !D.hrem || !D.hcl)
         return fail(MF_ENOMEM, "device allocation failed");
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
@@ -959,6 +1174,14 @@ int mf_stats_get(mf_graph *g, mf_stats *out) {
     out->n = g->n;
     out->m = g->m;
     out->arcs = g->A;
+    out->t_batch_ns = c.st[S_T_BATCH];
+    out->t_reset_ns = c.st[S_T_RESET];
+    out->t_bfs_ns = c.st[S_T_BFS];
+    out->t_pr_ns = c.st[S_T_PRW];
+    out->t_hub_ns = c.st[S_T_HUB];
+    out->t_ri_ns = c.st[S_T_RI];
+    out->hub_cycles = c.st[S_HUB_CYCLES];
+    out->barriers = c.st[S_BARRIERS];
     out->status = c.status;
     out->kernel_cycles = g->kc;
     out->grid_blocks = g->grid;

@@ -11,6 +11,11 @@ namespace mf {
 // kChunk-arc work items spread over all warps instead of by one warp.
 constexpr int kBigDeg = 1024;
 constexpr int kChunk = 1024;
+// Active vertices whose degree exceeds kHubDeg ("hubs") run PushRelabel and
+// RemoveInvalidEdges cooperatively over the whole grid, in kPrChunk-arc work
+// items; smaller ones are handled by one warp each.
+constexpr int kHubDeg = 512;
+constexpr int kPrChunk = 256;
 
 // Host image of the Bi-CSR of Sec. 5.1.  Vertex u owns arcs row[u] ..
 // row[u+1]-1, one per distinct neighbour v (u -> v edge, v -> u edge, or
@@ -28,6 +33,8 @@ struct HostBiCSR {
     std::vector<int32_t> arc_of_edge;
     int32_t cap_limit = 0;      // largest capacity one edge may take
     int64_t chunk_items = 0;    // sum over big vertices of ceil(deg / kChunk)
+    int64_t hubs = 0;           // vertices with degree > kHubDeg
+    int64_t hub_chunk_items = 0;  // sum over hubs of ceil(deg / kPrChunk)
     int32_t max_deg = 0;
 };
 
