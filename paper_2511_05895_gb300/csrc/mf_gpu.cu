@@ -64,6 +64,8 @@ struct Ctl {
     unsigned bar_gen;     // grid barrier generation
     int qcnt[3];          // (z) BFS frontier sizes, rotating by level
     int ccnt[3];          // (z) BFS chunk-item counts, rotating by level
+    int gtk[3];           // (z) BFS frontier-group tickets, rotating by level
+    int ctk[3];           // (z) BFS chunk-item tickets, rotating by level
     int wcnt;             // (z) active worklist size (vertices of degree <= kHubDeg)
     int hcnt;             // (z) active hub list size (degree > kHubDeg)
     int hccnt;            // (z) hub work items
@@ -173,7 +175,7 @@ __device__ __forceinline__ void warp_append(bool pred, int val, int *cnt, int *b
 
 // Bounded grid barrier for a cooperative (co-resident) grid.  Returns false
 // when any CTA gave up waiting (the kernel must then return).
-__device__ bool grid_sync(Ctl *C) {
+__device__ __forceinline__ bool grid_sync(Ctl *C) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned gen = ld_acquire(&C->bar_gen);
@@ -209,35 +211,51 @@ struct Counters {
               ri_moves = 0, clamped = 0, resat = 0;
 };
 
-// Backward BFS step over arc a of frontier vertex u (a in u's list, head v):
-// the arc v -> u is residual iff rr[a] > 0; an unvisited v (height n) gets
-// height L + 1 (global relabel, Sec. 2.2).  Newly reached vertices with
-// positive excess are active and join the worklist.  All 32 lanes call.
-__device__ __forceinline__ void bfs_visit(const DevGraph &G, bool valid, int a, int L, int *ncnt,
-                                          int *NF, Counters &K) {
-    bool disc = false;
-    int v = 0;
-    if (valid) {
-        v = __ldg(&G.head[a]);
-        const int rin = lcg(&G.rr[a]);
-        const int hv = lcg(&G.h[v]);
-        ++K.bfs_arcs;
-        if (rin > 0 && hv == G.n && v != G.s) disc = (atomicCAS(&G.h[v], G.n, L + 1) == G.n);
+constexpr int kIlp = 4;   // arcs in flight per lane in the BFS
+
+// Backward BFS step over kIlp arcs per lane (a[j] of frontier vertex u, head
+// v; ok[j] marks a real arc): the arc v -> u is residual iff rr[a] > 0; an
+// unvisited v (height n) gets height L + 1 (global relabel, Sec. 2.2).  Newly
+// reached vertices with positive excess are active and join the worklist
+// (degree <= kHubDeg) or the hub list.  Every load of a round is issued before
+// any of them is used.  All 32 lanes call.
+__device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kIlp], const bool (&ok)[kIlp],
+                                            int L, int *ncnt, int *NF, Counters &K) {
+    const int n = G.n;
+    int v[kIlp], rin[kIlp], hv[kIlp];
+    bool disc[kIlp];
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        v[j] = ok[j] ? __ldg(&G.head[a[j]]) : 0;
+        rin[j] = ok[j] ? lcg(&G.rr[a[j]]) : 0;
+        K.bfs_arcs += ok[j];
     }
-    warp_append(disc, v, ncnt, NF);
-    const bool act = disc && lcg(&G.e[v]) > 0;
-    if (__ballot_sync(kFull, act)) {
-        bool hub = false;
-        if (act) hub = __ldg(&G.row[v + 1]) - __ldg(&G.row[v]) > kHubDeg;
-        warp_append(act && !hub, v, &G.ctl->wcnt, G.wl);
-        warp_append(hub, v, &G.ctl->hcnt, G.hl);
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) hv[j] = (rin[j] > 0 && v[j] != G.s) ? lcg(&G.h[v[j]]) : -1;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) disc[j] = hv[j] == n && atomicCAS(&G.h[v[j]], n, L + 1) == n;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        warp_append(disc[j], v[j], ncnt, NF);
+        K.bfs_verts += disc[j];
     }
-    if (disc) ++K.bfs_verts;
+    bool act[kIlp];
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) act[j] = disc[j] && lcg(&G.e[v[j]]) > 0;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        if (__ballot_sync(kFull, act[j])) {
+            bool hub = false;
+            if (act[j]) hub = __ldg(&G.row[v[j] + 1]) - __ldg(&G.row[v[j]]) > kHubDeg;
+            warp_append(act[j] && !hub, v[j], &G.ctl->wcnt, G.wl);
+            warp_append(hub, v[j], &G.ctl->hcnt, G.hl);
+        }
+    }
 }
 
 // Expand up to 32 frontier vertices (one per lane, degree deg starting at
-// arc beg) with the arcs balanced over the lanes: lane i handles arc
-// k0 + i of the concatenated lists.
+// arc beg) with the arcs balanced over the lanes: lane i handles arcs
+// k0 + 32 j + i of the concatenated lists.
 __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int deg, int L,
                                                 int *ncnt, int *NF, Counters &K) {
     const int lane = threadIdx.x & 31;
@@ -249,18 +267,25 @@ __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int 
     }
     const int total = __shfl_sync(kFull, incl, 31);
     const int excl = incl - deg;
-    for (int k0 = 0; k0 < total; k0 += 32) {
-        const int k = k0 + lane;
-        int j = 0;  // owner lane: largest j with excl_j <= k
+    for (int k0 = 0; k0 < total; k0 += 32 * kIlp) {
+        int a[kIlp];
+        bool ok[kIlp];
 #pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            const int cand = j + step;
-            const int ex = __shfl_sync(kFull, excl, cand & 31);
-            if (cand < 32 && ex <= k) j = cand;
+        for (int jj = 0; jj < kIlp; ++jj) {
+            const int k = k0 + 32 * jj + lane;
+            int j = 0;  // owner lane: largest j with excl_j <= k
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int cand = j + step;
+                const int ex = __shfl_sync(kFull, excl, cand & 31);
+                if (cand < 32 && ex <= k) j = cand;
+            }
+            const int ob = __shfl_sync(kFull, beg, j);
+            const int oe = __shfl_sync(kFull, excl, j);
+            ok[jj] = k < total;
+            a[jj] = ob + (k - oe);
         }
-        const int ob = __shfl_sync(kFull, beg, j);
-        const int oe = __shfl_sync(kFull, excl, j);
-        bfs_visit(G, k < total, ob + (k - oe), L, ncnt, NF, K);
+        bfs_visit_n(G, a, ok, L, ncnt, NF, K);
     }
 }
 
@@ -276,6 +301,49 @@ __device__ __forceinline__ void push_arc(const DevGraph &G, int a, int v, int d)
     add_ll(&G.e[v], (long long)d);
 }
 
+// One round of a warp's arc scan: lane i holds arcs a0 + 32 j + i (j < kIlp)
+// with their residual (0 past `end`), head and the head's height.  All loads
+// of the round are issued before any is used.
+struct ArcRound {
+    int ra[kIlp], v[kIlp], hv[kIlp];
+};
+
+__device__ __forceinline__ void load_round(const DevGraph &G, int a0, int end, ArcRound &R) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        const int a = a0 + 32 * j + lane;
+        const bool ok = a < end;
+        R.ra[j] = ok ? lcg(&G.r[a]) : 0;
+        R.v[j] = ok ? __ldg(&G.head[a]) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) R.hv[j] = R.ra[j] > 0 ? lcg(&G.h[R.v[j]]) : 0;
+}
+
+__device__ __forceinline__ int round_arcs(int a0, int end) {
+    const int lane = threadIdx.x & 31;
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) c += (a0 + 32 * j + lane) < end;
+    return c;
+}
+
+// Lowest (height, arc offset from beg) key over the residual arcs of a round.
+__device__ __forceinline__ unsigned long long round_min_key(const ArcRound &R, int a0, int beg) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long best = ~0ull;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        if (R.ra[j] > 0) {
+            const unsigned long long key =
+                ((unsigned long long)(unsigned)R.hv[j] << 32) | (unsigned)(a0 + 32 * j + lane - beg);
+            best = key < best ? key : best;
+        }
+    }
+    return best;
+}
+
 // Algorithm 2 on vertex u by one warp, up to kc cycles.  A cycle scans u's
 // arcs once for the lowest residual neighbour height h^ (ties: lowest arc;
 // heights read once per cycle, Note 3 of Sec. 3).  If h(u) > h^ the cycle
@@ -284,7 +352,7 @@ __device__ __forceinline__ void push_arc(const DevGraph &G, int a, int v, int d)
 // second pass over the arcs; otherwise it relabels u to h^ + 1.  A vertex
 // without residual arcs gets height n.  Only u's warp lowers r(u, .) and e(u);
 // other warps only raise them, so every amount pushed is available.
-__device__ void push_relabel_warp(const DevGraph &G, int u, int kc, Counters &K) {
+__device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int kc, Counters &K) {
     const int lane = threadIdx.x & 31;
     const int n = G.n;
     const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
@@ -299,14 +367,12 @@ __device__ void push_relabel_warp(const DevGraph &G, int u, int kc, Counters &K)
         eu = __shfl_sync(kFull, eu, 0);
         if (hu >= n || eu <= 0) break;
         unsigned long long best = ~0ull;
-        for (int a = beg + lane; a < end; a += 32) {
-            const int ra = lcg(&G.r[a]);
-            ++K.pr_arcs;
-            if (ra > 0) {
-                const unsigned hv = (unsigned)lcg(&G.h[__ldg(&G.head[a])]);
-                const unsigned long long key = ((unsigned long long)hv << 32) | (unsigned)(a - beg);
-                best = key < best ? key : best;
-            }
+        for (int a0 = beg; a0 < end; a0 += 32 * kIlp) {
+            ArcRound R;
+            load_round(G, a0, end, R);
+            K.pr_arcs += round_arcs(a0, end);
+            const unsigned long long k = round_min_key(R, a0, beg);
+            best = k < best ? k : best;
         }
         best = warp_min(best);
         if (best == ~0ull) {
@@ -326,27 +392,24 @@ __device__ void push_relabel_warp(const DevGraph &G, int u, int kc, Counters &K)
             continue;
         }
         long long rem = eu, sent = 0;
-        for (int base = beg; base < end && rem > 0; base += 32) {
-            const int a = base + lane;
-            int ra = 0, v = 0;
-            if (a < end) {
-                ++K.pr_arcs;
-                ra = lcg(&G.r[a]);
-                if (ra > 0) {
-                    v = __ldg(&G.head[a]);
-                    if (lcg(&G.h[v]) != hh) ra = 0;
+        for (int a0 = beg; a0 < end && rem > 0; a0 += 32 * kIlp) {
+            ArcRound R;
+            load_round(G, a0, end, R);
+            K.pr_arcs += round_arcs(a0, end);
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                const int ra = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
+                const long long incl = warp_incl_scan(ra);
+                long long d = rem - (incl - ra);
+                d = d < 0 ? 0 : (d > ra ? ra : d);
+                if (d > 0) {
+                    push_arc(G, a0 + 32 * j + lane, R.v[j], (int)d);
+                    sent += d;
+                    ++K.push;
                 }
+                const long long tot = __shfl_sync(kFull, incl, 31);
+                rem -= tot < rem ? tot : rem;
             }
-            const long long incl = warp_incl_scan(ra);
-            long long d = rem - (incl - ra);
-            d = d < 0 ? 0 : (d > ra ? ra : d);
-            if (d > 0) {
-                push_arc(G, a, v, (int)d);
-                sent += d;
-                ++K.push;
-            }
-            const long long tot = __shfl_sync(kFull, incl, 31);
-            rem -= tot < rem ? tot : rem;
         }
         sent = warp_sum(sent);
         if (lane == 0 && sent) add_ll(&G.e[u], -sent);
@@ -354,24 +417,35 @@ __device__ void push_relabel_warp(const DevGraph &G, int u, int kc, Counters &K)
     }
 }
 
-// Algorithm 3 on vertex u by one warp: every residual arc u -> v with
-// h(u) > h(v) + 1 is saturated, moving its residual as excess to v.
-__device__ void remove_invalid_warp(const DevGraph &G, int u, Counters &K) {
+// Algorithm 3 over the arcs [a0, a1) of vertex u (height hu) by one warp:
+// every residual arc u -> v with h(u) > h(v) + 1 is saturated, moving its
+// residual as excess to v.  Returns this lane's share of the excess moved.
+__device__ __forceinline__ long long remove_invalid_range(const DevGraph &G, int hu, int a0, int a1,
+                                                          Counters &K) {
     const int lane = threadIdx.x & 31;
-    const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
-    const int hu = __shfl_sync(kFull, lane == 0 ? lcg(&G.h[u]) : 0, 0);
-    for (int a = beg + lane; a < end; a += 32) {
-        const int ra = lcg(&G.r[a]);
-        ++K.ri_arcs;
-        if (ra > 0) {
-            const int v = __ldg(&G.head[a]);
-            if (hu > lcg(&G.h[v]) + 1) {
-                push_arc(G, a, v, ra);
-                add_ll(&G.e[u], -(long long)ra);
+    long long moved = 0;
+    for (int b0 = a0; b0 < a1; b0 += 32 * kIlp) {
+        ArcRound R;
+        load_round(G, b0, a1, R);
+        K.ri_arcs += round_arcs(b0, a1);
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            if (R.ra[j] > 0 && hu > R.hv[j] + 1) {
+                push_arc(G, b0 + 32 * j + lane, R.v[j], R.ra[j]);
+                moved += R.ra[j];
                 ++K.ri_moves;
             }
         }
     }
+    return moved;
+}
+
+__device__ __forceinline__ void remove_invalid_warp(const DevGraph &G, int u, Counters &K) {
+    const int lane = threadIdx.x & 31;
+    const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
+    const int hu = __shfl_sync(kFull, lane == 0 ? lcg(&G.h[u]) : 0, 0);
+    const long long moved = warp_sum(remove_invalid_range(G, hu, beg, end, K));
+    if (lane == 0 && moved) add_ll(&G.e[u], -moved);
 }
 
 // ------------------------------------------------------------ the kernel --
@@ -519,6 +593,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             C->qcnt[1] = 0;
             C->qcnt[2] = 0;
             C->ccnt[0] = 0;
+            C->gtk[0] = C->ctk[0] = 0;
             C->wcnt = 0;
             C->hcnt = 0;
             C->hccnt = 0;
@@ -556,8 +631,15 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             if (gtid == 0) {
                 C->qcnt[(L + 2) % 3] = 0;
                 C->ccnt[(L + 1) % 3] = 0;
+                C->gtk[(L + 1) % 3] = 0;
+                C->ctk[(L + 1) % 3] = 0;
             }
-            for (int base = gwarp * 32; base < cur; base += nwarps * 32) {
+            // groups of 32 frontier vertices, handed out by an atomic ticket
+            for (;;) {
+                int grp = 0;
+                if (lane == 0) grp = atomicAdd(&C->gtk[L % 3], 1);
+                const int base = __shfl_sync(kFull, grp, 0) * 32;
+                if (base >= cur) break;
                 const int idx = base + lane;
                 int beg = 0, deg = 0;
                 if (idx < cur) {
@@ -576,10 +658,23 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             MF_SYNC(S_T_BFS);
             const int nch = lcg(ccnt);
             if (nch > 0) {
-                for (int c = gwarp; c < nch; c += nwarps) {
+                for (;;) {
+                    int c = 0;
+                    if (lane == 0) c = atomicAdd(&C->ctk[L % 3], 1);
+                    c = __shfl_sync(kFull, c, 0);
+                    if (c >= nch) break;
                     const int2 item = lcg(&G.cb[c]);
                     const int a1 = min(item.y + kChunk, __ldg(&G.row[item.x + 1]));
-                    for (int ab = item.y; ab < a1; ab += 32) bfs_visit(G, ab + lane < a1, ab + lane, L, ncnt, NF, K);
+                    for (int ab = item.y; ab < a1; ab += 32 * kIlp) {
+                        int a[kIlp];
+                        bool ok[kIlp];
+#pragma unroll
+                        for (int j = 0; j < kIlp; ++j) {
+                            a[j] = ab + 32 * j + lane;
+                            ok[j] = a[j] < a1;
+                        }
+                        bfs_visit_n(G, a, ok, L, ncnt, NF, K);
+                    }
                 }
                 MF_SYNC(S_T_BFS);
             }
@@ -632,14 +727,12 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
                     const int beg = __ldg(&G.row[u]);
                     const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
                     unsigned long long best = ~0ull;
-                    for (int a = item.y + lane; a < a1; a += 32) {
-                        const int ra = lcg(&G.r[a]);
-                        ++K.pr_arcs;
-                        if (ra > 0) {
-                            const unsigned hv = (unsigned)lcg(&G.h[__ldg(&G.head[a])]);
-                            const unsigned long long key = ((unsigned long long)hv << 32) | (unsigned)(a - beg);
-                            best = key < best ? key : best;
-                        }
+                    for (int a0 = item.y; a0 < a1; a0 += 32 * kIlp) {
+                        ArcRound R;
+                        load_round(G, a0, a1, R);
+                        K.pr_arcs += round_arcs(a0, a1);
+                        const unsigned long long k = round_min_key(R, a0, beg);
+                        best = k < best ? k : best;
                     }
                     best = warp_min(best);
                     if (lane == 0 && best != ~0ull) atomicMin(&G.hkey[item.x], best);
@@ -686,19 +779,18 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
                     const int u = lcg(&G.hl[item.x]);
                     const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
                     long long sent = 0;
-                    for (int base = item.y; base < a1; base += 32) {
-                        const int a = base + lane;
-                        int ra = 0, v = 0;
-                        if (a < a1) {
-                            ++K.pr_arcs;
-                            ra = lcg(&G.r[a]);
-                            if (ra > 0) {
-                                v = __ldg(&G.head[a]);
-                                if (lcg(&G.h[v]) != hh) ra = 0;
-                            }
+                    for (int a0 = item.y; a0 < a1; a0 += 32 * kIlp) {
+                        ArcRound R;
+                        load_round(G, a0, a1, R);
+                        K.pr_arcs += round_arcs(a0, a1);
+                        int ra[kIlp];
+                        long long incl[kIlp], tot = 0;
+#pragma unroll
+                        for (int j = 0; j < kIlp; ++j) {
+                            ra[j] = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
+                            incl[j] = warp_incl_scan(ra[j]) + tot;   // arc order: round j, then lane
+                            tot = __shfl_sync(kFull, incl[j], 31);
                         }
-                        const long long incl = warp_incl_scan(ra);
-                        const long long tot = __shfl_sync(kFull, incl, 31);
                         if (tot == 0) continue;
                         long long old = 0;
                         if (lane == 0)
@@ -706,12 +798,15 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
                                                        (unsigned long long)(-tot));
                         old = __shfl_sync(kFull, old, 0);
                         if (old <= 0) break;
-                        long long d = old - (incl - ra);
-                        d = d < 0 ? 0 : (d > ra ? ra : d);
-                        if (d > 0) {
-                            push_arc(G, a, v, (int)d);
-                            sent += d;
-                            ++K.push;
+#pragma unroll
+                        for (int j = 0; j < kIlp; ++j) {
+                            long long d = old - (incl[j] - ra[j]);
+                            d = d < 0 ? 0 : (d > ra[j] ? ra[j] : d);
+                            if (d > 0) {
+                                push_arc(G, a0 + 32 * j + lane, R.v[j], (int)d);
+                                sent += d;
+                                ++K.push;
+                            }
                         }
                     }
                     sent = warp_sum(sent);
@@ -731,20 +826,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             const int u = lcg(&G.hl[item.x]);
             const int hu = lcg(&G.h[u]);
             const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
-            long long moved = 0;
-            for (int a = item.y + lane; a < a1; a += 32) {
-                const int ra = lcg(&G.r[a]);
-                ++K.ri_arcs;
-                if (ra > 0) {
-                    const int v = __ldg(&G.head[a]);
-                    if (hu > lcg(&G.h[v]) + 1) {
-                        push_arc(G, a, v, ra);
-                        moved += ra;
-                        ++K.ri_moves;
-                    }
-                }
-            }
-            moved = warp_sum(moved);
+            const long long moved = warp_sum(remove_invalid_range(G, hu, item.y, a1, K));
             if (lane == 0 && moved) add_ll(&G.e[u], -moved);
         }
         MF_SYNC(S_T_RI);
@@ -754,7 +836,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
     if (gtid == 0) {
         C->flow = lcg(&G.e[t]) + lcg(&C->dacc[it & 1]);
         C->iters = it;
-        for (int i = 0; i < 3; ++i) C->qcnt[i] = C->ccnt[i] = 0;
+        for (int i = 0; i < 3; ++i) C->qcnt[i] = C->ccnt[i] = C->gtk[i] = C->ctk[i] = 0;
         C->wcnt = C->hcnt = C->hccnt = 0;
         C->hub_act[0] = C->hub_act[1] = 0;
         C->dacc[0] = C->dacc[1] = 0;
