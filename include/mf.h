@@ -99,7 +99,8 @@ typedef struct mf_options {
  *               batch + re-saturation, height init, BFS, warp PushRelabel,
  *               hub PushRelabel cycles, RemoveInvalidEdges
  *  hub_cycles   cooperative PushRelabel cycles of high-degree vertices
- *  barriers     grid barriers passed */
+ *  barriers     grid barriers passed
+ *  bfs_bottom_up_levels  BFS levels run bottom-up (direction-optimising) */
 typedef struct mf_stats {
     int64_t flow;
     int64_t iterations;
@@ -126,6 +127,7 @@ typedef struct mf_stats {
     int64_t t_ri_ns;
     int64_t hub_cycles;
     int64_t barriers;
+    int64_t bfs_bottom_up_levels;
     int32_t status;
     int32_t kernel_cycles;
     int32_t grid_blocks;

@@ -38,7 +38,7 @@
 
 namespace mf {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = 768;   // one CTA per SM: 152 arrivals per grid barrier
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned long long kWaitNs = 20ull * 1000ull * 1000ull * 1000ull;  // 20 s per barrier wait
 
@@ -66,6 +66,7 @@ struct Ctl {
     int ccnt[3];          // (z) BFS chunk-item counts, rotating by level
     int gtk[3];           // (z) BFS frontier-group tickets, rotating by level
     int ctk[3];           // (z) BFS chunk-item tickets, rotating by level
+    long long asum[3];    // (z) sum of the degrees of each BFS frontier, rotating
     int wcnt;             // (z) active worklist size (vertices of degree <= kHubDeg)
     int hcnt;             // (z) active hub list size (degree > kHubDeg)
     int hccnt;            // (z) hub work items
@@ -84,6 +85,7 @@ enum Stat {
     S_BATCH, S_CLAMPED, S_RESAT,
     // phase times (ns, globaltimer of CTA 0 between grid barriers) and counts
     S_T_BATCH, S_T_RESET, S_T_BFS, S_T_PRW, S_T_HUB, S_T_RI, S_HUB_CYCLES, S_BARRIERS,
+    S_BU_LEVELS,
     S_COUNT
 };
 static_assert(S_COUNT <= S_COUNT_MAX, "statistics array too small");
@@ -213,6 +215,34 @@ struct Counters {
 
 constexpr int kIlp = 4;   // arcs in flight per lane in the BFS
 
+struct ArcRoundBfs {
+    int ra[kIlp], w[kIlp];
+};
+
+// Bookkeeping of a vertex v reached at the next level (disc): it joins the
+// next frontier, its degree counts towards that frontier's arc total, and
+// with positive excess it is active: worklist (degree <= kHubDeg) or hub
+// list.  All 32 lanes call.
+__device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int v, int *ncnt, int *NF,
+                                               long long *asum, Counters &K) {
+    warp_append(disc, v, ncnt, NF);
+    if (!__ballot_sync(kFull, disc)) return;
+    int deg = 0;
+    bool act = false;
+    if (disc) {
+        deg = __ldg(&G.row[v + 1]) - __ldg(&G.row[v]);
+        act = lcg(&G.e[v]) > 0;
+        ++K.bfs_verts;
+    }
+    const long long ds = warp_sum((long long)deg);
+    if ((threadIdx.x & 31) == 0 && ds) add_ll(asum, ds);
+    if (__ballot_sync(kFull, act)) {
+        const bool hub = act && deg > kHubDeg;
+        warp_append(act && !hub, v, &G.ctl->wcnt, G.wl);
+        warp_append(hub, v, &G.ctl->hcnt, G.hl);
+    }
+}
+
 // Backward BFS step over kIlp arcs per lane (a[j] of frontier vertex u, head
 // v; ok[j] marks a real arc): the arc v -> u is residual iff rr[a] > 0; an
 // unvisited v (height n) gets height L + 1 (global relabel, Sec. 2.2).  Newly
@@ -220,7 +250,7 @@ constexpr int kIlp = 4;   // arcs in flight per lane in the BFS
 // (degree <= kHubDeg) or the hub list.  Every load of a round is issued before
 // any of them is used.  All 32 lanes call.
 __device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kIlp], const bool (&ok)[kIlp],
-                                            int L, int *ncnt, int *NF, Counters &K) {
+                                            int L, int *ncnt, int *NF, long long *asum, Counters &K) {
     const int n = G.n;
     int v[kIlp], rin[kIlp], hv[kIlp];
     bool disc[kIlp];
@@ -235,29 +265,14 @@ __device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kI
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) disc[j] = hv[j] == n && atomicCAS(&G.h[v[j]], n, L + 1) == n;
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
-        warp_append(disc[j], v[j], ncnt, NF);
-        K.bfs_verts += disc[j];
-    }
-    bool act[kIlp];
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) act[j] = disc[j] && lcg(&G.e[v[j]]) > 0;
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
-        if (__ballot_sync(kFull, act[j])) {
-            bool hub = false;
-            if (act[j]) hub = __ldg(&G.row[v[j] + 1]) - __ldg(&G.row[v[j]]) > kHubDeg;
-            warp_append(act[j] && !hub, v[j], &G.ctl->wcnt, G.wl);
-            warp_append(hub, v[j], &G.ctl->hcnt, G.hl);
-        }
-    }
+    for (int j = 0; j < kIlp; ++j) bfs_discovered(G, disc[j], v[j], ncnt, NF, asum, K);
 }
 
 // Expand up to 32 frontier vertices (one per lane, degree deg starting at
 // arc beg) with the arcs balanced over the lanes: lane i handles arcs
 // k0 + 32 j + i of the concatenated lists.
 __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int deg, int L,
-                                                int *ncnt, int *NF, Counters &K) {
+                                                int *ncnt, int *NF, long long *asum, Counters &K) {
     const int lane = threadIdx.x & 31;
     int incl = deg;
 #pragma unroll
@@ -285,8 +300,102 @@ __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int 
             ok[jj] = k < total;
             a[jj] = ob + (k - oe);
         }
-        bfs_visit_n(G, a, ok, L, ncnt, NF, K);
+        bfs_visit_n(G, a, ok, L, ncnt, NF, asum, K);
     }
+}
+
+// Bottom-up step of the backward BFS (direction-optimising search): the
+// unvisited vertices v of a group of 32 consecutive ids look for a residual
+// arc v -> w into the current frontier (h(w) == L); the first one found gives
+// h(v) = L + 1.  The group's arcs are balanced over the lanes and the scan of
+// a vertex stops once it is found.  Vertices of degree > kBigDeg become
+// kChunk-arc items of the chunk list instead.  All 32 lanes call.
+__device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base, int L, int *ncnt, int *NF,
+                                                    long long *asum, int *ccnt, Counters &K) {
+    const int lane = threadIdx.x & 31;
+    const int n = G.n;
+    const int v = base + lane;
+    int beg = 0, deg = 0;
+    if (v < n && v != G.s && lcg(&G.h[v]) == n) {
+        beg = __ldg(&G.row[v]);
+        deg = __ldg(&G.row[v + 1]) - beg;
+        if (deg > kBigDeg) {
+            const int nc = (deg + kChunk - 1) / kChunk;
+            const int pos = atomicAdd(ccnt, nc);
+            for (int c = 0; c < nc; ++c) G.cb[pos + c] = make_int2(v, beg + c * kChunk);
+            deg = 0;
+        }
+    }
+    const unsigned want = __ballot_sync(kFull, deg > 0);
+    unsigned found = 0;
+    if (want) {
+        int incl = deg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - deg;
+        for (int k0 = 0; k0 < total && found != want; k0 += 32 * kIlp) {
+            int a[kIlp], own[kIlp], ra[kIlp], w[kIlp];
+#pragma unroll
+            for (int jj = 0; jj < kIlp; ++jj) {
+                const int k = k0 + 32 * jj + lane;
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int cand = j + step;
+                    const int ex = __shfl_sync(kFull, excl, cand & 31);
+                    if (cand < 32 && ex <= k) j = cand;
+                }
+                own[jj] = j;
+                a[jj] = __shfl_sync(kFull, beg, j) + (k - __shfl_sync(kFull, excl, j));
+                const bool live = k < total && !((found >> j) & 1u);
+                ra[jj] = live ? lcg(&G.r[a[jj]]) : 0;
+                w[jj] = live ? __ldg(&G.head[a[jj]]) : 0;
+                K.bfs_arcs += live;
+            }
+            unsigned hit = 0;
+#pragma unroll
+            for (int jj = 0; jj < kIlp; ++jj)
+                if (ra[jj] > 0 && lcg(&G.h[w[jj]]) == L) hit |= 1u << own[jj];
+            found |= __reduce_or_sync(kFull, hit);
+        }
+    }
+    const bool disc = (found >> lane) & 1u;
+    if (disc) G.h[v] = L + 1;
+    bfs_discovered(G, disc, v, ncnt, NF, asum, K);
+}
+
+// Bottom-up scan of one kChunk-arc item of a high-degree unvisited vertex;
+// several items of one vertex may find a parent, the height CAS elects one.
+__device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item, int L, int *ncnt, int *NF,
+                                                   long long *asum, Counters &K) {
+    const int lane = threadIdx.x & 31;
+    const int v = item.x;
+    bool disc = false;
+    if (lcg(&G.h[v]) == G.n) {
+        const int a1 = min(item.y + kChunk, __ldg(&G.row[v + 1]));
+        bool hit = false;
+        for (int a0 = item.y; a0 < a1 && !hit; a0 += 32 * kIlp) {
+            ArcRoundBfs R;
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                const int a = a0 + 32 * j + lane;
+                R.ra[j] = a < a1 ? lcg(&G.r[a]) : 0;
+                R.w[j] = a < a1 ? __ldg(&G.head[a]) : 0;
+                K.bfs_arcs += a < a1;
+            }
+            bool mine = false;
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) mine |= R.ra[j] > 0 && lcg(&G.h[R.w[j]]) == L;
+            hit = __any_sync(kFull, mine);
+        }
+        if (hit && lane == 0) disc = atomicCAS(&G.h[v], G.n, L + 1) == G.n;
+    }
+    disc = __shfl_sync(kFull, disc, 0);
+    bfs_discovered(G, disc && lane == 0, v, ncnt, NF, asum, K);
 }
 
 // ------------------------------------------------------ push / relabel --
@@ -462,7 +571,7 @@ __device__ __forceinline__ void remove_invalid_warp(const DevGraph &G, int u, Co
         }                                                                     \
     } while (0)
 
-__global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
+__global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     Ctl *C = G.ctl;
     const int lane = threadIdx.x & 31;
     const long long gtid = (long long)blockIdx.x * kBlock + threadIdx.x;
@@ -594,6 +703,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             C->qcnt[2] = 0;
             C->ccnt[0] = 0;
             C->gtk[0] = C->ctk[0] = 0;
+            C->asum[1] = C->asum[2] = 0;
             C->wcnt = 0;
             C->hcnt = 0;
             C->hccnt = 0;
@@ -602,7 +712,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
             if (gtimer() - C->t_start > J.time_limit_ns) C->abort_loop = 1;
         }
         {
-            long long dsum = 0;
+            long long dsum = 0, rdeg = 0;
             for (long long vb = (long long)gwarp * 32; vb < n; vb += gthreads) {
                 const long long v = vb + lane;
                 bool root = false;
@@ -611,49 +721,76 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
                     root = (v == t) || (v != s && ev < 0);
                     G.h[v] = root ? 0 : n;
                     if (root && v != t) dsum += ev;
+                    if (root) rdeg += __ldg(&G.row[v + 1]) - __ldg(&G.row[v]);
                 }
                 warp_append(root, (int)v, &C->qcnt[0], G.qb0);
             }
             dsum = warp_sum(dsum);
+            rdeg = warp_sum(rdeg);
             if (lane == 0 && dsum) add_ll(&C->dacc[par], dsum);
+            if (lane == 0 && rdeg) add_ll(&C->asum[0], rdeg);
         }
         MF_SYNC(S_T_RESET);
 
-        // backward BFS from the sinks over residual arcs (global relabel)
+        // backward BFS from the sinks over residual arcs (global relabel),
+        // level-synchronous and direction-optimising: top-down from the
+        // frontier while it is small, bottom-up from the unvisited vertices
+        // while the frontier holds more than 1/14 of the unvisited arcs.
         int L = 0;
+        bool bottom_up = false;
+        long long arcs_seen = 0;
         for (;;) {
             const int cur = lcg(&C->qcnt[L % 3]);
             if (cur == 0) break;
+            const long long mf = lcg(&C->asum[L % 3]);
+            arcs_seen += mf;
+            if (!bottom_up) bottom_up = mf * 14 > G.A - arcs_seen && cur * 64LL > n;
+            else bottom_up = cur * 24LL >= n;
             const int *F = (L & 1) ? G.qb1 : G.qb0;
             int *NF = (L & 1) ? G.qb0 : G.qb1;
             int *ncnt = &C->qcnt[(L + 1) % 3];
             int *ccnt = &C->ccnt[L % 3];
+            long long *asum = &C->asum[(L + 1) % 3];
             if (gtid == 0) {
                 C->qcnt[(L + 2) % 3] = 0;
                 C->ccnt[(L + 1) % 3] = 0;
                 C->gtk[(L + 1) % 3] = 0;
                 C->ctk[(L + 1) % 3] = 0;
+                C->asum[(L + 2) % 3] = 0;
+                if (bottom_up) C->st[S_BU_LEVELS] += 1;
             }
-            // groups of 32 frontier vertices, handed out by an atomic ticket
-            for (;;) {
-                int grp = 0;
-                if (lane == 0) grp = atomicAdd(&C->gtk[L % 3], 1);
-                const int base = __shfl_sync(kFull, grp, 0) * 32;
-                if (base >= cur) break;
-                const int idx = base + lane;
-                int beg = 0, deg = 0;
-                if (idx < cur) {
-                    const int u = lcg(&F[idx]);
-                    beg = __ldg(&G.row[u]);
-                    deg = __ldg(&G.row[u + 1]) - beg;
-                    if (deg > kBigDeg) {
-                        const int nc = (deg + kChunk - 1) / kChunk;
-                        const int pos = atomicAdd(ccnt, nc);
-                        for (int c = 0; c < nc; ++c) G.cb[pos + c] = make_int2(u, beg + c * kChunk);
-                        deg = 0;
-                    }
+            if (bottom_up) {
+                // groups of 32 consecutive vertex ids, handed out by an atomic ticket
+                const int groups = (n + 31) / 32;
+                for (;;) {
+                    int grp = 0;
+                    if (lane == 0) grp = atomicAdd(&C->gtk[L % 3], 1);
+                    grp = __shfl_sync(kFull, grp, 0);
+                    if (grp >= groups) break;
+                    bfs_bottom_up_group(G, grp * 32, L, ncnt, NF, asum, ccnt, K);
                 }
-                bfs_expand_warp(G, beg, deg, L, ncnt, NF, K);
+            } else {
+                // groups of 32 frontier vertices, handed out by an atomic ticket
+                for (;;) {
+                    int grp = 0;
+                    if (lane == 0) grp = atomicAdd(&C->gtk[L % 3], 1);
+                    const int base = __shfl_sync(kFull, grp, 0) * 32;
+                    if (base >= cur) break;
+                    const int idx = base + lane;
+                    int beg = 0, deg = 0;
+                    if (idx < cur) {
+                        const int u = lcg(&F[idx]);
+                        beg = __ldg(&G.row[u]);
+                        deg = __ldg(&G.row[u + 1]) - beg;
+                        if (deg > kBigDeg) {
+                            const int nc = (deg + kChunk - 1) / kChunk;
+                            const int pos = atomicAdd(ccnt, nc);
+                            for (int c = 0; c < nc; ++c) G.cb[pos + c] = make_int2(u, beg + c * kChunk);
+                            deg = 0;
+                        }
+                    }
+                    bfs_expand_warp(G, beg, deg, L, ncnt, NF, asum, K);
+                }
             }
             MF_SYNC(S_T_BFS);
             const int nch = lcg(ccnt);
@@ -664,6 +801,10 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
                     c = __shfl_sync(kFull, c, 0);
                     if (c >= nch) break;
                     const int2 item = lcg(&G.cb[c]);
+                    if (bottom_up) {
+                        bfs_bottom_up_item(G, item, L, ncnt, NF, asum, K);
+                        continue;
+                    }
                     const int a1 = min(item.y + kChunk, __ldg(&G.row[item.x + 1]));
                     for (int ab = item.y; ab < a1; ab += 32 * kIlp) {
                         int a[kIlp];
@@ -673,7 +814,7 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
                             a[j] = ab + 32 * j + lane;
                             ok[j] = a[j] < a1;
                         }
-                        bfs_visit_n(G, a, ok, L, ncnt, NF, K);
+                        bfs_visit_n(G, a, ok, L, ncnt, NF, asum, K);
                     }
                 }
                 MF_SYNC(S_T_BFS);
@@ -698,7 +839,10 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
 
         // PushRelabel (Alg. 2): one warp per worklist vertex ...
         for (int i = gwarp; i < nw; i += nwarps) push_relabel_warp(G, lcg(&G.wl[i]), J.kc, K);
-        if (gtid == 0) C->qcnt[0] = 0;
+        if (gtid == 0) {
+            C->qcnt[0] = 0;
+            C->asum[0] = 0;
+        }
         // ... and the hubs together, kPrChunk-arc items over the whole grid
         int nhc = 0;
         if (nh > 0) {
@@ -836,7 +980,10 @@ __global__ void __launch_bounds__(kBlock) k_solve(DevGraph G, Job J) {
     if (gtid == 0) {
         C->flow = lcg(&G.e[t]) + lcg(&C->dacc[it & 1]);
         C->iters = it;
-        for (int i = 0; i < 3; ++i) C->qcnt[i] = C->ccnt[i] = C->gtk[i] = C->ctk[i] = 0;
+        for (int i = 0; i < 3; ++i) {
+            C->qcnt[i] = C->ccnt[i] = C->gtk[i] = C->ctk[i] = 0;
+            C->asum[i] = 0;
+        }
         C->wcnt = C->hcnt = C->hccnt = 0;
         C->hub_act[0] = C->hub_act[1] = 0;
         C->dacc[0] = C->dacc[1] = 0;
@@ -1264,6 +1411,7 @@ int mf_stats_get(mf_graph *g, mf_stats *out) {
     out->t_ri_ns = c.st[S_T_RI];
     out->hub_cycles = c.st[S_HUB_CYCLES];
     out->barriers = c.st[S_BARRIERS];
+    out->bfs_bottom_up_levels = c.st[S_BU_LEVELS];
     out->status = c.status;
     out->kernel_cycles = g->kc;
     out->grid_blocks = g->grid;

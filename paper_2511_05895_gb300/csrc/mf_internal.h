@@ -7,10 +7,12 @@
 
 namespace mf {
 
-// Vertices whose Bi-CSR degree exceeds kBigDeg are expanded by the BFS as
-// kChunk-arc work items spread over all warps instead of by one warp.
-constexpr int kBigDeg = 1024;
-constexpr int kChunk = 1024;
+// Frontier vertices whose Bi-CSR degree exceeds kBigDeg are expanded by the
+// BFS as kChunk-arc work items spread over all warps instead of inside their
+// 32-vertex group, so that no warp holds more than 32 x kBigDeg arcs of a
+// level.
+constexpr int kBigDeg = 64;
+constexpr int kChunk = 256;
 // Active vertices whose degree exceeds kHubDeg ("hubs") run PushRelabel and
 // RemoveInvalidEdges cooperatively over the whole grid, in kPrChunk-arc work
 // items; smaller ones are handled by one warp each.
