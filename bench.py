@@ -251,7 +251,7 @@ def main():
     G.sync()
     stats_acc = {k: 0 for k in [b for b in BYTES if b != "height_init"] +
                  ["iterations", "bfs_levels", "t_batch_ns", "t_reset_ns", "t_bfs_ns", "t_pr_ns",
-                  "t_hub_ns", "t_ri_ns", "hub_cycles", "barriers", "bfs_bottom_up_levels"]}
+                  "t_hub_ns", "t_ri_ns", "hub_cycles", "barriers", "bfs_bottom_up_levels", "pr_rounds"]}
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()

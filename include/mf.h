@@ -100,7 +100,9 @@ typedef struct mf_options {
  *               hub PushRelabel cycles, RemoveInvalidEdges
  *  hub_cycles   cooperative PushRelabel cycles of high-degree vertices
  *  barriers     grid barriers passed
- *  bfs_bottom_up_levels  BFS levels run bottom-up (direction-optimising) */
+ *  bfs_bottom_up_levels  BFS levels run bottom-up (direction-optimising)
+ *  pr_rounds    PushRelabel activation rounds (vertices made active by a push
+ *               are processed in the next round of the same iteration) */
 typedef struct mf_stats {
     int64_t flow;
     int64_t iterations;
@@ -128,6 +130,7 @@ typedef struct mf_stats {
     int64_t hub_cycles;
     int64_t barriers;
     int64_t bfs_bottom_up_levels;
+    int64_t pr_rounds;
     int32_t status;
     int32_t kernel_cycles;
     int32_t grid_blocks;

@@ -35,7 +35,7 @@ class Stats(ctypes.Structure):
         "flow", "iterations", "bfs_levels", "bfs_vertices", "bfs_arcs", "worklist", "pr_arcs",
         "pushes", "relabels", "ri_arcs", "ri_moves", "batch", "clamped", "resat_arcs", "n", "m",
         "arcs", "t_batch_ns", "t_reset_ns", "t_bfs_ns", "t_pr_ns", "t_hub_ns", "t_ri_ns",
-        "hub_cycles", "barriers", "bfs_bottom_up_levels")] + [(f, ctypes.c_int32) for f in ("status", "kernel_cycles", "grid_blocks",
+        "hub_cycles", "barriers", "bfs_bottom_up_levels", "pr_rounds")] + [(f, ctypes.c_int32) for f in ("status", "kernel_cycles", "grid_blocks",
                                                    "block_threads")]
 
     def as_dict(self):

@@ -51,6 +51,9 @@ constexpr int ST_STICKY = ST_ITERS | ST_WAIT | ST_TIME;
 
 enum JobKind { JOB_SOLVE = 0, JOB_REPAIR = 1, JOB_RECOMPUTE = 2 };
 
+// PushRelabel activation rounds per loop iteration (see k_solve).
+constexpr int kMaxRounds = 16;
+
 constexpr int S_COUNT_MAX = 24;
 
 // Device control block.  Fields marked (z) are zero whenever no k_solve is
@@ -67,6 +70,10 @@ struct Ctl {
     int gtk[3];           // (z) BFS frontier-group tickets, rotating by level
     int ctk[3];           // (z) BFS chunk-item tickets, rotating by level
     long long asum[3];    // (z) sum of the degrees of each BFS frontier, rotating
+    int acnt[3];          // (z) activation-round list sizes, rotating by round
+    int rlcnt;            // (z) relabel list size
+    int rtk[3];           // (z) activation-round tickets, rotating by round
+    unsigned stamp_base;  // first activation stamp of the next launch (kept across launches)
     int wcnt;             // (z) active worklist size (vertices of degree <= kHubDeg)
     int hcnt;             // (z) active hub list size (degree > kHubDeg)
     int hccnt;            // (z) hub work items
@@ -85,7 +92,7 @@ enum Stat {
     S_BATCH, S_CLAMPED, S_RESAT,
     // phase times (ns, globaltimer of CTA 0 between grid barriers) and counts
     S_T_BATCH, S_T_RESET, S_T_BFS, S_T_PRW, S_T_HUB, S_T_RI, S_HUB_CYCLES, S_BARRIERS,
-    S_BU_LEVELS,
+    S_BU_LEVELS, S_ROUNDS,
     S_COUNT
 };
 static_assert(S_COUNT <= S_COUNT_MAX, "statistics array too small");
@@ -104,6 +111,9 @@ struct DevGraph {
     int2 *hcl;                // hub work items (hub index, first arc)
     unsigned long long *hkey; // per-hub lowest (height, arc) key
     long long *hrem;          // per-hub excess left to push in the current cycle
+    unsigned *astamp;         // per-vertex stamp of the last activation list joined
+    unsigned *rstamp;         // per-vertex stamp of the last relabel list joined
+    int *rl;                  // vertices relabelled in the current loop iteration
     Ctl *ctl;
 };
 
@@ -401,13 +411,44 @@ __device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item,
 // ------------------------------------------------------ push / relabel --
 // One push of d units along arc a (u -> v): both residual copies of the arc
 // pair and the head's excess; the caller subtracts the total from e(u).
-__device__ __forceinline__ void push_arc(const DevGraph &G, int a, int v, int d) {
+__device__ __forceinline__ long long push_arc(const DevGraph &G, int a, int v, int d) {
     const int b = __ldg(&G.rev[a]);
     atomicSub(&G.r[a], d);
     atomicSub(&G.rr[b], d);
     atomicAdd(&G.r[b], d);
     atomicAdd(&G.rr[a], d);
-    add_ll(&G.e[v], (long long)d);
+    return (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&G.e[v]), (unsigned long long)d);
+}
+
+// Where the vertices that a push makes active go: the list of the next
+// activation round (see the PushRelabel phase of k_solve).  A vertex enters
+// one list at most once, by the stamp of that list.
+struct ActList {
+    int *cnt;
+    int *list;
+    unsigned stamp;
+    unsigned rstamp;   // stamp of this loop iteration's relabel list
+};
+
+// A vertex whose height PushRelabel raised joins the relabel list of the loop
+// iteration once: only relabelled vertices can own arcs that RemoveInvalidEdges
+// must saturate (the others keep their BFS height, which no residual arc can
+// make steep).  One thread calls.
+__device__ __forceinline__ void note_relabel(const DevGraph &G, int u, unsigned rstamp) {
+    if (atomicExch(&G.rstamp[u], rstamp) != rstamp) G.rl[atomicAdd(&G.ctl->rlcnt, 1)] = u;
+}
+
+// A push of d units raised e(v) from `old`: if v turned active (excess
+// positive, below height n, not s or t, degree <= kHubDeg) it joins the next
+// activation round.  All 32 lanes call.
+__device__ __forceinline__ void note_activation(const DevGraph &G, bool pushed, int v, long long old, long long d,
+                                                const ActList &AL) {
+    bool add = false;
+    if (pushed && old <= 0 && old + d > 0 && v != G.s && v != G.t) {
+        if (lcg(&G.h[v]) < G.n && __ldg(&G.row[v + 1]) - __ldg(&G.row[v]) <= kHubDeg)
+            add = atomicExch(&G.astamp[v], AL.stamp) != AL.stamp;
+    }
+    warp_append(add, v, AL.cnt, AL.list);
 }
 
 // One round of a warp's arc scan: lane i holds arcs a0 + 32 j + i (j < kIlp)
@@ -461,7 +502,8 @@ __device__ __forceinline__ unsigned long long round_min_key(const ArcRound &R, i
 // second pass over the arcs; otherwise it relabels u to h^ + 1.  A vertex
 // without residual arcs gets height n.  Only u's warp lowers r(u, .) and e(u);
 // other warps only raise them, so every amount pushed is available.
-__device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int kc, Counters &K) {
+__device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int kc, const ActList &AL,
+                                                  Counters &K) {
     const int lane = threadIdx.x & 31;
     const int n = G.n;
     const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
@@ -488,6 +530,7 @@ __device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int 
             if (lane == 0) {
                 G.h[u] = n;
                 ++K.relabel;
+                note_relabel(G, u, AL.rstamp);
             }
             break;
         }
@@ -496,6 +539,7 @@ __device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int 
             if (lane == 0) {
                 G.h[u] = hh + 1;
                 ++K.relabel;
+                note_relabel(G, u, AL.rstamp);
             }
             __syncwarp();
             continue;
@@ -511,11 +555,13 @@ __device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int 
                 const long long incl = warp_incl_scan(ra);
                 long long d = rem - (incl - ra);
                 d = d < 0 ? 0 : (d > ra ? ra : d);
+                long long old = 0;
                 if (d > 0) {
-                    push_arc(G, a0 + 32 * j + lane, R.v[j], (int)d);
+                    old = push_arc(G, a0 + 32 * j + lane, R.v[j], (int)d);
                     sent += d;
                     ++K.push;
                 }
+                note_activation(G, d > 0, R.v[j], old, d, AL);
                 const long long tot = __shfl_sync(kFull, incl, 31);
                 rem -= tot < rem ? tot : rem;
             }
@@ -585,6 +631,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     // A sticky error (iteration cap, barrier wait) invalidates the state
     // until the next mf_solve, which clears it before launching.
     if (__ldcg(&C->status) & ST_STICKY) return;
+    const unsigned stamp_base = __ldcg(&C->stamp_base) + 1u;
     if (gtid == 0) {
         for (int i = 0; i < S_COUNT; ++i) C->st[i] = 0;
         C->st[S_BATCH] = J.kind == JOB_SOLVE ? 0 : J.k;
@@ -704,6 +751,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             C->ccnt[0] = 0;
             C->gtk[0] = C->ctk[0] = 0;
             C->asum[1] = C->asum[2] = 0;
+            C->acnt[0] = C->acnt[1] = C->acnt[2] = 0;
+            C->rtk[0] = C->rtk[1] = C->rtk[2] = 0;
+            C->rlcnt = 0;
             C->wcnt = 0;
             C->hcnt = 0;
             C->hccnt = 0;
@@ -835,15 +885,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             if (gtid == 0) atomicOr(&C->status, ST_TIME);
             break;
         }
-        if (gtid == 0) C->st[S_WL] += nw + nh;
+        if (gtid == 0) C->st[S_WL] += nh;
 
-        // PushRelabel (Alg. 2): one warp per worklist vertex ...
-        for (int i = gwarp; i < nw; i += nwarps) push_relabel_warp(G, lcg(&G.wl[i]), J.kc, K);
+        // PushRelabel (Alg. 2).  High-degree vertices first, together in
+        // kPrChunk-arc items over the whole grid; then the worklist, one warp
+        // per vertex, in activation rounds: a vertex that a push turns active
+        // joins the list of the next round instead of waiting for the next
+        // BFS.  Rounds are separated by grid barriers, so no vertex is ever
+        // processed by two warps at once.
+        const unsigned sbase = stamp_base + (unsigned)it * (kMaxRounds + 1);
         if (gtid == 0) {
             C->qcnt[0] = 0;
             C->asum[0] = 0;
         }
-        // ... and the hubs together, kPrChunk-arc items over the whole grid
+        const ActList AL0{&C->wcnt, G.wl, sbase, sbase};
         int nhc = 0;
         if (nh > 0) {
             for (int i = gwarp; i < nh; i += nwarps) {
@@ -859,7 +914,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 pos = __shfl_sync(kFull, pos, 0);
                 for (int c = lane; c < nc; c += 32) G.hcl[pos + c] = make_int2(i, beg + c * kPrChunk);
             }
-            MF_SYNC(S_T_PRW);
+            MF_SYNC(S_T_HUB);
             nhc = lcg(&C->hccnt);
             for (int c = 0; c < J.kc; ++c) {
                 if (gtid == 0) C->st[S_HUB_CYCLES] += 1;
@@ -946,11 +1001,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         for (int j = 0; j < kIlp; ++j) {
                             long long d = old - (incl[j] - ra[j]);
                             d = d < 0 ? 0 : (d > ra[j] ? ra[j] : d);
+                            long long prev = 0;
                             if (d > 0) {
-                                push_arc(G, a0 + 32 * j + lane, R.v[j], (int)d);
+                                prev = push_arc(G, a0 + 32 * j + lane, R.v[j], (int)d);
                                 sent += d;
                                 ++K.push;
                             }
+                            note_activation(G, d > 0, R.v[j], prev, d, AL0);
                         }
                     }
                     sent = warp_sum(sent);
@@ -959,12 +1016,36 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 MF_SYNC(S_T_HUB);
                 if (lcg(&C->hub_act[c & 1]) == 0) break;
             }
-        } else {
-            MF_SYNC(S_T_PRW);
+        }
+        {
+            int cnt = lcg(&C->wcnt);
+            const int *list = G.wl;
+            for (int rd = 0;; ++rd) {
+                int *nlist = (rd & 1) ? G.qb0 : G.qb1;
+                const ActList AL{&C->acnt[(rd + 1) % 3], nlist, sbase + (unsigned)rd + 1, sbase};
+                if (gtid == 0) {
+                    C->acnt[(rd + 2) % 3] = 0;
+                    C->rtk[(rd + 1) % 3] = 0;
+                    C->st[S_ROUNDS] += 1;
+                    C->st[S_WL] += cnt;
+                }
+                for (;;) {
+                    int i = 0;
+                    if (lane == 0) i = atomicAdd(&C->rtk[rd % 3], 1);
+                    i = __shfl_sync(kFull, i, 0);
+                    if (i >= cnt) break;
+                    push_relabel_warp(G, lcg(&list[i]), J.kc, AL, K);
+                }
+                MF_SYNC(S_T_PRW);
+                cnt = lcg(AL.cnt);
+                list = nlist;
+                if (cnt == 0 || rd + 1 >= kMaxRounds) break;
+            }
         }
 
-        // RemoveInvalidEdges (Alg. 3): worklist vertices by warps, hubs by items
-        for (int i = gwarp; i < nw; i += nwarps) remove_invalid_warp(G, lcg(&G.wl[i]), K);
+        // RemoveInvalidEdges (Alg. 3): relabelled vertices by warps, hubs by items
+        const int nrl = lcg(&C->rlcnt);
+        for (int i = gwarp; i < nrl; i += nwarps) remove_invalid_warp(G, lcg(&G.rl[i]), K);
         for (int w = gwarp; w < nhc; w += nwarps) {
             const int2 item = lcg(&G.hcl[w]);
             const int u = lcg(&G.hl[item.x]);
@@ -984,7 +1065,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             C->qcnt[i] = C->ccnt[i] = C->gtk[i] = C->ctk[i] = 0;
             C->asum[i] = 0;
         }
-        C->wcnt = C->hcnt = C->hccnt = 0;
+        C->wcnt = C->hcnt = C->hccnt = C->rlcnt = 0;
+        C->acnt[0] = C->acnt[1] = C->acnt[2] = 0;
+        C->rtk[0] = C->rtk[1] = C->rtk[2] = 0;
+        C->stamp_base = stamp_base + (unsigned)(it + 1) * (kMaxRounds + 1);
         C->hub_act[0] = C->hub_act[1] = 0;
         C->dacc[0] = C->dacc[1] = 0;
         C->batch_err = 0;
@@ -1258,11 +1342,14 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     D.hkey = dnew<unsigned long long>(g, NH);
     D.hrem = dnew<long long>(g, NH);
     D.hcl = dnew<int2>(g, size_t(std::max<int64_t>(H.hub_chunk_items, 1)));
+    D.astamp = dnew<unsigned>(g, N);
+    D.rstamp = dnew<unsigned>(g, N);
+    D.rl = dnew<int>(g, N);
     D.ctl = dnew<Ctl>(g, 1);
     g->side_buf = dnew<unsigned char>(g, N);
     if (!row || !head || !rev || !aoe || !D.cap || !D.r || !D.rr || !D.h || !D.e || !D.cap_edge || !D.stamp ||
         !D.qb0 || !D.qb1 || !D.wl || !D.cb || !D.ctl || !g->side_buf || !D.hl || !D.hmode || !D.hkey ||
-        !D.hrem || !D.hcl)
+        !D.hrem || !D.hcl || !D.astamp || !D.rstamp || !D.rl)
         return fail(MF_ENOMEM, "device allocation failed");
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
@@ -1273,6 +1360,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
         up(D.cap, H.cap.data(), size_t(H.arcs) * 4) || up(D.cap_edge, cap_edge.data(), size_t(m) * 4) ||
         cudaMemsetAsync(D.stamp, 0, M * 4, st) || cudaMemsetAsync(D.ctl, 0, sizeof(Ctl), st) ||
         cudaMemsetAsync(D.e, 0, N * 8, st) || cudaMemsetAsync(D.h, 0, N * 4, st) ||
+        cudaMemsetAsync(D.astamp, 0, N * 4, st) || cudaMemsetAsync(D.rstamp, 0, N * 4, st) ||
         cudaMemsetAsync(D.r, 0, A * 4, st) || cudaMemsetAsync(D.rr, 0, A * 4, st) ||
         cudaStreamSynchronize(st)) {
         cudaGetLastError();
@@ -1302,6 +1390,8 @@ int mf_solve(mf_graph *g, void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     MF_CUDA(cudaSetDevice(g->dev));
     MF_CUDA(cudaMemsetAsync(g->dg.ctl, 0, sizeof(Ctl), st));
+    MF_CUDA(cudaMemsetAsync(g->dg.astamp, 0, size_t(g->n) * 4, st));
+    MF_CUDA(cudaMemsetAsync(g->dg.rstamp, 0, size_t(g->n) * 4, st));
     Job j{};
     j.kind = JOB_SOLVE;
     j.kc = g->kc;
@@ -1412,6 +1502,7 @@ int mf_stats_get(mf_graph *g, mf_stats *out) {
     out->hub_cycles = c.st[S_HUB_CYCLES];
     out->barriers = c.st[S_BARRIERS];
     out->bfs_bottom_up_levels = c.st[S_BU_LEVELS];
+    out->pr_rounds = c.st[S_ROUNDS];
     out->status = c.status;
     out->kernel_cycles = g->kc;
     out->grid_blocks = g->grid;
