@@ -40,6 +40,7 @@ namespace mf {
 
 constexpr int kBlock = 768;   // one CTA per SM: 152 arrivals per grid barrier
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kFlagStride = 8;   // one 32-byte sector per CTA arrival flag
 constexpr unsigned long long kWaitNs = 20ull * 1000ull * 1000ull * 1000ull;  // 20 s per barrier wait
 
 // status bits (Ctl::status)
@@ -63,7 +64,6 @@ struct Ctl {
     int status;           // ST_* bits                      } read together by
     int batch_err;        // (z) set by batch validation    } mf_flow_value
     long long flow;       // result of the last solve/repair }
-    unsigned bar_count;   // grid barrier arrivals (z)
     unsigned bar_gen;     // grid barrier generation
     int qcnt[3];          // (z) BFS frontier sizes, rotating by level
     int ccnt[3];          // (z) BFS chunk-item counts, rotating by level
@@ -108,9 +108,11 @@ struct DevGraph {
     int *qb0, *qb1, *wl;
     int2 *cb;
     int *hl, *hmode;          // active hubs; per-hub cycle state
+    int *hnit, *hdone;        // per-hub work items, and items finished in the cycle
     int2 *hcl;                // hub work items (hub index, first arc)
     unsigned long long *hkey; // per-hub lowest (height, arc) key
     long long *hrem;          // per-hub excess left to push in the current cycle
+    unsigned *bar_flags;      // grid barrier arrival flags, kFlagStride words per CTA
     unsigned *astamp;         // per-vertex stamp of the last activation list joined
     unsigned *rstamp;         // per-vertex stamp of the last relabel list joined
     int *rl;                  // vertices relabelled in the current loop iteration
@@ -185,22 +187,32 @@ __device__ __forceinline__ void warp_append(bool pred, int val, int *cnt, int *b
     if (pred) buf[base + __popc(mask & ((1u << lane) - 1u))] = val;
 }
 
-// Bounded grid barrier for a cooperative (co-resident) grid.  Returns false
-// when any CTA gave up waiting (the kernel must then return).
-__device__ __forceinline__ bool grid_sync(Ctl *C) {
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded grid barrier for a cooperative (co-resident) grid.  Arrival is one
+// release store per CTA into its own flag word (no contended atomic); the
+// threads of CTA 0 poll all flags in parallel and then release the new
+// generation, which the other CTAs poll.  Every wait gives up after kWaitNs
+// and sets ST_WAIT; returns false when any CTA gave up (the kernel must then
+// return).
+__device__ __forceinline__ bool grid_sync(Ctl *C, unsigned *flags) {
+    __shared__ unsigned s_gen;
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned gen = ld_acquire(&C->bar_gen);
+        s_gen = gen;
         __threadfence();
-        const unsigned arrived = atomicAdd(&C->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&C->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&C->bar_gen, 1u);
-        } else {
+        st_release(&flags[blockIdx.x * kFlagStride], gen + 1);
+    }
+    __syncthreads();
+    const unsigned next = s_gen + 1;
+    if (blockIdx.x == 0) {
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
             const unsigned long long t0 = gtimer();
             unsigned spins = 0;
-            while (ld_acquire(&C->bar_gen) == gen) {
+            while (ld_acquire(&flags[b * kFlagStride]) != next) {
                 if ((++spins & 31u) == 0) {
                     if (__ldcg(&C->status) & ST_WAIT) break;
                     if (gtimer() - t0 > kWaitNs) {
@@ -208,8 +220,26 @@ __device__ __forceinline__ bool grid_sync(Ctl *C) {
                         break;
                     }
                 }
-                __nanosleep(40);
+                __nanosleep(20);
             }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(&C->bar_gen, next);
+        }
+    } else if (threadIdx.x == 0) {
+        const unsigned long long t0 = gtimer();
+        unsigned spins = 0;
+        while (ld_acquire(&C->bar_gen) != next) {
+            if ((++spins & 31u) == 0) {
+                if (__ldcg(&C->status) & ST_WAIT) break;
+                if (gtimer() - t0 > kWaitNs) {
+                    atomicOr(&C->status, ST_WAIT);
+                    break;
+                }
+            }
+            __nanosleep(20);
         }
         __threadfence();
     }
@@ -608,7 +638,7 @@ __device__ __forceinline__ void remove_invalid_warp(const DevGraph &G, int u, Co
 // previous barrier to a phase bucket of the statistics.
 #define MF_SYNC(bucket)                                                       \
     do {                                                                      \
-        if (!grid_sync(C)) return;                                            \
+        if (!grid_sync(C, G.bar_flags)) return;                               \
         if (gtid == 0) {                                                      \
             const unsigned long long now_ = gtimer();                         \
             C->st[bucket] += (long long)(now_ - tprev);                       \
@@ -659,7 +689,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         }
         MF_SYNC(S_T_BATCH);
         if (lcg(&C->batch_err)) {
-            grid_sync(C);
+            grid_sync(C, G.bar_flags);
             if (gtid == 0) {
                 atomicOr(&C->status, ST_EINVAL);
                 C->batch_err = 0;
@@ -910,6 +940,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     pos = atomicAdd(&C->hccnt, nc);
                     G.hkey[i] = ~0ull;
                     G.hmode[i] = 0;
+                    G.hnit[i] = nc;
+                    G.hdone[i] = 0;
                 }
                 pos = __shfl_sync(kFull, pos, 0);
                 for (int c = lane; c < nc; c += 32) G.hcl[pos + c] = make_int2(i, beg + c * kPrChunk);
@@ -918,11 +950,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             nhc = lcg(&C->hccnt);
             for (int c = 0; c < J.kc; ++c) {
                 if (gtid == 0) C->st[S_HUB_CYCLES] += 1;
-                // H1: lowest residual neighbour of every unfinished hub
+                // H1: lowest residual neighbour of every unfinished hub; the
+                // warp that completes a hub's last item takes the hub's
+                // decision (push at the lowest height, relabel, or finish)
                 for (int w = gwarp; w < nhc; w += nwarps) {
                     const int2 item = lcg(&G.hcl[w]);
-                    if (lcg(&G.hmode[item.x]) < 0) continue;
-                    const int u = lcg(&G.hl[item.x]);
+                    const int i = item.x;
+                    if (lcg(&G.hmode[i]) < 0) continue;
+                    const int u = lcg(&G.hl[i]);
                     const int beg = __ldg(&G.row[u]);
                     const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
                     unsigned long long best = ~0ull;
@@ -934,40 +969,43 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         best = k < best ? k : best;
                     }
                     best = warp_min(best);
-                    if (lane == 0 && best != ~0ull) atomicMin(&G.hkey[item.x], best);
-                }
-                MF_SYNC(S_T_HUB);
-                // H2: per hub, push at the lowest height, relabel, or finish
-                for (long long i = gtid; i < nh; i += gthreads) {
-                    if (lcg(&G.hmode[i]) < 0) continue;
-                    const int u = lcg(&G.hl[i]);
-                    const int hu = lcg(&G.h[u]);
-                    const long long eu = lcg(&G.e[u]);
-                    const unsigned long long key = __ldcg(&G.hkey[i]);
-                    G.hkey[i] = ~0ull;
-                    int mode;
-                    if (hu >= n || eu <= 0) {
-                        mode = -1;
-                    } else if (key == ~0ull) {
-                        G.h[u] = n;
-                        ++K.relabel;
-                        mode = -1;
-                    } else {
-                        const int hh = (int)(key >> 32);
-                        if (hu > hh) {
-                            mode = hh + 1;          // push to the arcs at height hh
-                            G.hrem[i] = eu;
-                        } else {
-                            G.h[u] = hh + 1;
-                            ++K.relabel;
-                            mode = 0;
+                    if (lane == 0) {
+                        if (best != ~0ull) atomicMin(&G.hkey[i], best);
+                        __threadfence();
+                        if (atomicAdd(&G.hdone[i], 1) == lcg(&G.hnit[i]) - 1) {
+                            __threadfence();
+                            const int hu = lcg(&G.h[u]);
+                            const long long eu = lcg(&G.e[u]);
+                            const unsigned long long key = __ldcg(&G.hkey[i]);
+                            G.hkey[i] = ~0ull;
+                            G.hdone[i] = 0;
+                            int mode;
+                            if (hu >= n || eu <= 0) {
+                                mode = -1;
+                            } else if (key == ~0ull) {
+                                G.h[u] = n;
+                                ++K.relabel;
+                                mode = -1;
+                            } else {
+                                const int hh = (int)(key >> 32);
+                                if (hu > hh) {
+                                    mode = hh + 1;          // push to the arcs at height hh
+                                    G.hrem[i] = eu;
+                                } else {
+                                    G.h[u] = hh + 1;
+                                    ++K.relabel;
+                                    mode = 0;
+                                }
+                            }
+                            G.hmode[i] = mode;
+                            if (mode >= 0) atomicAdd(&C->hub_act[c & 1], 1);
                         }
                     }
-                    G.hmode[i] = mode;
-                    if (mode >= 0) atomicAdd(&C->hub_act[c & 1], 1);
                 }
-                if (gtid == 0) C->hub_act[(c + 1) & 1] = 0;
                 MF_SYNC(S_T_HUB);
+                // hub_act[(c+1)&1] was last read by the exit test of cycle c-1,
+                // which every thread has passed once it is past the H1 barrier
+                if (gtid == 0) C->hub_act[(c + 1) & 1] = 0;
                 // H3: pushes along the lowest arcs; each warp reserves its share
                 // of the hub's excess with one atomic
                 for (int w = gwarp; w < nhc; w += nwarps) {
@@ -1341,7 +1379,10 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     D.hmode = dnew<int>(g, NH);
     D.hkey = dnew<unsigned long long>(g, NH);
     D.hrem = dnew<long long>(g, NH);
+    D.hnit = dnew<int>(g, NH);
+    D.hdone = dnew<int>(g, NH);
     D.hcl = dnew<int2>(g, size_t(std::max<int64_t>(H.hub_chunk_items, 1)));
+    D.bar_flags = dnew<unsigned>(g, size_t(g->grid) * kFlagStride);
     D.astamp = dnew<unsigned>(g, N);
     D.rstamp = dnew<unsigned>(g, N);
     D.rl = dnew<int>(g, N);
@@ -1349,7 +1390,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     g->side_buf = dnew<unsigned char>(g, N);
     if (!row || !head || !rev || !aoe || !D.cap || !D.r || !D.rr || !D.h || !D.e || !D.cap_edge || !D.stamp ||
         !D.qb0 || !D.qb1 || !D.wl || !D.cb || !D.ctl || !g->side_buf || !D.hl || !D.hmode || !D.hkey ||
-        !D.hrem || !D.hcl || !D.astamp || !D.rstamp || !D.rl)
+        !D.hrem || !D.hnit || !D.hdone || !D.hcl || !D.astamp || !D.rstamp || !D.rl || !D.bar_flags)
         return fail(MF_ENOMEM, "device allocation failed");
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
@@ -1359,6 +1400,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
         up(rev, H.rev.data(), size_t(H.arcs) * 4) || up(aoe, H.arc_of_edge.data(), size_t(m) * 4) ||
         up(D.cap, H.cap.data(), size_t(H.arcs) * 4) || up(D.cap_edge, cap_edge.data(), size_t(m) * 4) ||
         cudaMemsetAsync(D.stamp, 0, M * 4, st) || cudaMemsetAsync(D.ctl, 0, sizeof(Ctl), st) ||
+        cudaMemsetAsync(D.bar_flags, 0, size_t(g->grid) * kFlagStride * 4, st) ||
         cudaMemsetAsync(D.e, 0, N * 8, st) || cudaMemsetAsync(D.h, 0, N * 4, st) ||
         cudaMemsetAsync(D.astamp, 0, N * 4, st) || cudaMemsetAsync(D.rstamp, 0, N * 4, st) ||
         cudaMemsetAsync(D.r, 0, A * 4, st) || cudaMemsetAsync(D.rr, 0, A * 4, st) ||
@@ -1390,6 +1432,7 @@ int mf_solve(mf_graph *g, void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     MF_CUDA(cudaSetDevice(g->dev));
     MF_CUDA(cudaMemsetAsync(g->dg.ctl, 0, sizeof(Ctl), st));
+    MF_CUDA(cudaMemsetAsync(g->dg.bar_flags, 0, size_t(g->grid) * kFlagStride * 4, st));
     MF_CUDA(cudaMemsetAsync(g->dg.astamp, 0, size_t(g->n) * 4, st));
     MF_CUDA(cudaMemsetAsync(g->dg.rstamp, 0, size_t(g->n) * 4, st));
     Job j{};
@@ -1559,6 +1602,7 @@ int mf_import_state(mf_graph *g, const int32_t *r, const int64_t *excess, const 
     for (int32_t v = 0; v < g->n; ++v)
         if (v != g->s && v != g->t && he[size_t(v)] < 0) flow += he[size_t(v)];
     MF_CUDA(cudaMemset(g->dg.ctl, 0, sizeof(Ctl)));
+    MF_CUDA(cudaMemset(g->dg.bar_flags, 0, size_t(g->grid) * kFlagStride * 4));
     MF_CUDA(cudaMemcpy(&g->dg.ctl->flow, &flow, sizeof(flow), cudaMemcpyHostToDevice));
     MF_CUDA(cudaDeviceSynchronize());
     g->solved = true;
