@@ -224,6 +224,38 @@ int mf_import_state(mf_graph *g, const int32_t *r, const int64_t *excess, const 
 /* Free all device memory of the graph (synchronises first).  NULL is a no-op. */
 void mf_destroy(mf_graph *g);
 
+/* Allocation-free static max-flow on a Bi-CSR that the caller already holds in
+ * device memory.  The paper has no counterpart: it is for callers that must
+ * not allocate GPU memory themselves -- for example a plugin that runs inside
+ * another framework which owns all device memory through its own pool, or a
+ * service path where allocations are forbidden after start-up -- and so
+ * cannot use mf_create.  Instead of allocating, it works in one static
+ * device array of 12,976,640 bytes (about 12.4 MiB) that every GPU which
+ * loads this library holds until the process exits.
+ *   n, arcs        vertices (2 .. 131072) and Bi-CSR arcs (0 .. 2097152);
+ *                  larger graphs are rejected with MF_EINVAL
+ *   row [n+1], head/rev/cap [arcs]   the Bi-CSR of mf_bicsr_host, int32,
+ *                  device memory, read only
+ *   s, t           source and sink
+ *   kernel_cycles  as mf_options (0 = default)
+ *   r [arcs] int32, excess [n] int64, height [n] int32: device outputs --
+ *                  the final residuals, excesses and heights (the min cut is
+ *                  {v : height[v] >= n})
+ *   flow           HOST int64 receiving the max-flow value
+ *   stream         stream for the work (NULL = legacy default stream)
+ * Synchronises `stream` and returns MF_OK, MF_EINVAL, MF_ECUDA or
+ * MF_ETIMEOUT.  It calls no cudaMalloc or cudaFree.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and the
+ * kernel's grid size; make that first call before any stream capture.  All
+ * calls share the one array and it keeps the last call's contents (each call
+ * clears what must start at zero): calls that overlap on the GPU -- from
+ * several host threads or on several streams -- race and must be serialised
+ * by the caller. */
+int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const int32_t *head,
+                           const int32_t *rev, const int32_t *cap, int32_t s, int32_t t,
+                           int32_t kernel_cycles, int32_t *r, int64_t *excess, int32_t *height,
+                           int64_t *flow, void *stream);
+
 /* Static string naming an error code. */
 const char *mf_strerror(int code);
 

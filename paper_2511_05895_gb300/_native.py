@@ -46,7 +46,7 @@ class Stats(ctypes.Structure):
 EXPORTED = ["mf_options_default", "mf_create", "mf_cap_limit", "mf_solve", "mf_apply_updates",
             "mf_sync", "mf_flow_value", "mf_min_cut", "mf_stats_get", "mf_sizes",
             "mf_export_graph", "mf_export_state", "mf_import_state", "mf_destroy",
-            "mf_strerror", "mf_version", "mf_last_error", "mf_bicsr_host"]
+            "mf_strerror", "mf_version", "mf_last_error", "mf_bicsr_host", "mf_solve_bicsr_noalloc"]
 
 
 class MFError(RuntimeError):
@@ -90,6 +90,7 @@ def lib(build_if_missing: bool = False):
         "mf_version": ([], ctypes.c_char_p),
         "mf_last_error": ([], ctypes.c_char_p),
         "mf_bicsr_host": ([i32, i64, P, P, P, i32, i32, P, P, P, P, P, P, P], ctypes.c_int),
+        "mf_solve_bicsr_noalloc": ([i32, i64, P, P, P, P, i32, i32, i32, P, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

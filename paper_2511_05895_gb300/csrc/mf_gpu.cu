@@ -29,6 +29,7 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1126,6 +1127,43 @@ __global__ void k_cut_side(const int *h, int n, unsigned char *side) {
         side[v] = h[v] >= n ? 1 : 0;
 }
 
+// ---------------------------------------------- allocation-free solve --
+// Scratch of mf_solve_bicsr_noalloc: one static device array per GPU that
+// loads this library, used instead of device allocations for everything the
+// solve kernel needs besides the caller's graph and output arrays.  Sized for
+// graphs of at most kNoAllocMaxN vertices and kNoAllocMaxArcs Bi-CSR arcs.
+constexpr int kNoAllocMaxN = 1 << 17;
+constexpr long long kNoAllocMaxArcs = 1LL << 21;
+constexpr int kNoAllocMaxGrid = 1024;
+constexpr long long kNoAllocMaxHubs = kNoAllocMaxArcs / kHubDeg;
+
+__host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Byte offsets of the scratch regions (each 256-byte aligned).
+struct NoAllocLayout {
+    static constexpr size_t ctl = 0;
+    static constexpr size_t flags = ctl + align256(sizeof(Ctl));
+    static constexpr size_t rr = flags + align256(sizeof(unsigned) * kNoAllocMaxGrid * kFlagStride);
+    static constexpr size_t qb0 = rr + align256(sizeof(int) * kNoAllocMaxArcs);
+    static constexpr size_t qb1 = qb0 + align256(sizeof(int) * kNoAllocMaxN);
+    static constexpr size_t wl = qb1 + align256(sizeof(int) * kNoAllocMaxN);
+    static constexpr size_t rl = wl + align256(sizeof(int) * kNoAllocMaxN);
+    static constexpr size_t astamp = rl + align256(sizeof(int) * kNoAllocMaxN);
+    static constexpr size_t rstamp = astamp + align256(sizeof(unsigned) * kNoAllocMaxN);
+    static constexpr size_t cb = rstamp + align256(sizeof(unsigned) * kNoAllocMaxN);
+    static constexpr size_t hcl = cb + align256(sizeof(int2) * (kNoAllocMaxArcs / kChunk + kNoAllocMaxN));
+    static constexpr size_t hl = hcl + align256(sizeof(int2) * (kNoAllocMaxArcs / kPrChunk + kNoAllocMaxHubs));
+    static constexpr size_t hmode = hl + align256(sizeof(int) * kNoAllocMaxHubs);
+    static constexpr size_t hnit = hmode + align256(sizeof(int) * kNoAllocMaxHubs);
+    static constexpr size_t hdone = hnit + align256(sizeof(int) * kNoAllocMaxHubs);
+    static constexpr size_t hkey = hdone + align256(sizeof(int) * kNoAllocMaxHubs);
+    static constexpr size_t hrem = hkey + align256(sizeof(unsigned long long) * kNoAllocMaxHubs);
+    static constexpr size_t total = hrem + align256(sizeof(long long) * kNoAllocMaxHubs);
+};
+
+static_assert(NoAllocLayout::total == 12976640, "the header states the scratch size (12,976,640 bytes)");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NoAllocLayout::total];
+
 }  // namespace mf
 
 // =============================================================== C ABI ====
@@ -1154,6 +1192,16 @@ struct mf_graph {
 namespace {
 
 thread_local std::string g_last_error;
+
+// Per-device set-up of the allocation-free solve.
+constexpr int kNoAllocMaxDevices = 64;
+struct NoAllocDevice {
+    unsigned char *base = nullptr;   // device address of g_noalloc_scratch
+    int grid = 0;
+    cudaError_t err = cudaSuccess;
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::once_flag g_noalloc_once[kNoAllocMaxDevices];
 
 int set_err(int code, const std::string &msg) {
     g_last_error = msg;
@@ -1616,6 +1664,85 @@ void mf_destroy(mf_graph *g) {
     cudaDeviceSynchronize();
     for (void *p : g->owned) dfree(g, p);
     delete g;
+}
+
+// Allocation-free static solve on a caller-provided Bi-CSR (see mf.h).
+int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const int32_t *head, const int32_t *rev,
+                           const int32_t *cap, int32_t s, int32_t t, int32_t kernel_cycles, int32_t *r,
+                           int64_t *excess, int32_t *height, int64_t *flow, void *stream) {
+    if (n < 2 || s < 0 || t < 0 || s >= n || t >= n || s == t || arcs < 0)
+        return set_err(MF_EINVAL, "bad sizes or terminals");
+    if (n > kNoAllocMaxN || arcs > kNoAllocMaxArcs)
+        return set_err(MF_EINVAL, "graph larger than the static scratch: at most " + std::to_string(kNoAllocMaxN) +
+                                      " vertices and " + std::to_string(kNoAllocMaxArcs) + " arcs");
+    if (!row || !head || !rev || !cap || !r || !excess || !height || !flow)
+        return set_err(MF_EINVAL, "null argument");
+    int dev = 0;
+    MF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return set_err(MF_EINVAL, "device index out of range");
+    // once per device: the device address of the static scratch array (host
+    // code only sees a host-side stand-in for it) and the co-resident grid
+    std::call_once(g_noalloc_once[dev], [dev]() {
+        NoAllocDevice &D = g_noalloc_dev[dev];
+        D.err = cudaGetSymbolAddress(reinterpret_cast<void **>(&D.base), g_noalloc_scratch);
+        int per_sm = 0, sms = 0;
+        if (D.err == cudaSuccess) D.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (D.err == cudaSuccess)
+            D.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, kBlock, 0);
+        D.grid = std::min(per_sm * sms, kNoAllocMaxGrid);
+        if (D.err == cudaSuccess && D.grid < 1) D.err = cudaErrorInvalidConfiguration;
+    });
+    const NoAllocDevice &ND = g_noalloc_dev[dev];
+    if (ND.err != cudaSuccess)
+        return set_err(MF_ECUDA, std::string("scratch set-up: ") + cudaGetErrorString(ND.err));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char *b = ND.base;
+    using Lo = NoAllocLayout;
+    DevGraph D{};
+    D.n = n; D.s = s; D.t = t; D.m = 0; D.A = arcs; D.cap_limit = 0;
+    D.row = row; D.head = head; D.rev = rev; D.arc_of_edge = nullptr;
+    D.cap = const_cast<int *>(cap);      // read only by a solve from zero flow
+    D.r = r; D.e = reinterpret_cast<long long *>(excess); D.h = height;
+    D.cap_edge = nullptr; D.stamp = nullptr;
+    D.ctl = reinterpret_cast<Ctl *>(b + Lo::ctl);
+    D.bar_flags = reinterpret_cast<unsigned *>(b + Lo::flags);
+    D.rr = reinterpret_cast<int *>(b + Lo::rr);
+    D.qb0 = reinterpret_cast<int *>(b + Lo::qb0);
+    D.qb1 = reinterpret_cast<int *>(b + Lo::qb1);
+    D.wl = reinterpret_cast<int *>(b + Lo::wl);
+    D.rl = reinterpret_cast<int *>(b + Lo::rl);
+    D.astamp = reinterpret_cast<unsigned *>(b + Lo::astamp);
+    D.rstamp = reinterpret_cast<unsigned *>(b + Lo::rstamp);
+    D.cb = reinterpret_cast<int2 *>(b + Lo::cb);
+    D.hcl = reinterpret_cast<int2 *>(b + Lo::hcl);
+    D.hl = reinterpret_cast<int *>(b + Lo::hl);
+    D.hmode = reinterpret_cast<int *>(b + Lo::hmode);
+    D.hnit = reinterpret_cast<int *>(b + Lo::hnit);
+    D.hdone = reinterpret_cast<int *>(b + Lo::hdone);
+    D.hkey = reinterpret_cast<unsigned long long *>(b + Lo::hkey);
+    D.hrem = reinterpret_cast<long long *>(b + Lo::hrem);
+    // the previous call's contents stay in the array: clear what must start at 0
+    MF_CUDA(cudaMemsetAsync(D.ctl, 0, sizeof(Ctl), st));
+    MF_CUDA(cudaMemsetAsync(D.bar_flags, 0, sizeof(unsigned) * kNoAllocMaxGrid * kFlagStride, st));
+    MF_CUDA(cudaMemsetAsync(D.astamp, 0, sizeof(unsigned) * size_t(n), st));
+    MF_CUDA(cudaMemsetAsync(D.rstamp, 0, sizeof(unsigned) * size_t(n), st));
+    Job j{};
+    j.kind = JOB_SOLVE;
+    j.kc = kernel_cycles > 0 ? kernel_cycles : int(std::max<int64_t>(1, (arcs / 2 + n / 2) / n));
+    j.max_iters = 4LL * n + 1000;
+    j.time_limit_ns = 60ull * 1000ull * 1000ull * 1000ull;
+    void *args[] = {&D, &j};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_solve, dim3(ND.grid), dim3(kBlock), args, 0, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(MF_ECUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
+    }
+    int32_t status = 0;
+    MF_CUDA(cudaMemcpyAsync(&status, &D.ctl->status, sizeof(status), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaMemcpyAsync(flow, &D.ctl->flow, sizeof(*flow), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    if (status & ST_STICKY) return set_err(MF_ETIMEOUT, "device loop did not finish");
+    return MF_OK;
 }
 
 }  // extern "C"
