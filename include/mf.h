@@ -230,7 +230,7 @@ void mf_destroy(mf_graph *g);
  * another framework which owns all device memory through its own pool, or a
  * service path where allocations are forbidden after start-up -- and so
  * cannot use mf_create.  Instead of allocating, it works in one static
- * device array of 12,976,640 bytes (about 12.4 MiB) that every GPU which
+ * device array of 12,943,872 bytes (about 12.3 MiB) that every GPU which
  * loads this library holds until the process exits.
  *   n, arcs        vertices (2 .. 131072) and Bi-CSR arcs (0 .. 2097152);
  *                  larger graphs are rejected with MF_EINVAL
