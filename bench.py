@@ -187,10 +187,66 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def serving_measurement(rate_per_s: float, duration_s: float, seed: int = 5) -> dict:
+    """Serving loop on a mix of resident graphs (RMAT 16 and 18, a 1024^2
+    segmentation grid, a unit bipartite graph of 2^18 + 2^18 vertices): Poisson
+    arrivals at `rate_per_s`, batch sizes log-uniform in [100, 100k] (at most
+    a tenth of the graph's edges), served by mf_server with per-graph grids of
+    19 to 38 CTAs.  Reports p50/p99 submit-to-completion latency and the
+    completed batches per second."""
+    from paper_2511_05895_gb300 import MaxFlowGraph, Server
+    specs = [(gen.rmat(scale=16, seed=301), 19), (gen.rmat(scale=18, seed=302), 38),
+             (gen.grid_segmentation(1024, 1024, seed=303), 38),
+             (gen.bipartite(1 << 18, 1 << 18, 1 << 22, seed=304), 38)]
+    S = Server()
+    Gs, caps = [], []
+    for g, grid in specs:
+        G = MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=4, grid_blocks=grid)
+        G.solve()
+        G.flow_value()
+        S.add_graph(G, 100_000)
+        Gs.append(G)
+        caps.append(g.cap.copy())
+    rng = np.random.default_rng(seed)
+    n_req = max(8, int(rate_per_s * duration_s))
+    plan = []
+    for i in range(n_req):
+        gi = int(rng.integers(len(specs)))
+        g = specs[gi][0]
+        k = int(np.exp(rng.uniform(np.log(100), np.log(min(100_000, g.m // 10)))))
+        if g.meta.get("kind") == "grid":
+            b = gen.grid_rect_batch(g, seed=seed, index=i, side_lo=16, side_hi=max(17, int(np.sqrt(k / 2))))
+        else:
+            hi = 1 if g.meta.get("kind") == "bipartite" else 500
+            b = gen.mixed_batch(caps[gi], k, 1, hi, seed=seed, index=i)
+        gen.apply_batch(caps[gi], b)
+        plan.append((gi, b))
+    gaps = rng.exponential(1.0 / rate_per_s, n_req)
+    S.reset_stats()
+    t0 = time.perf_counter()
+    t_next = t0
+    for (gi, b), gap in zip(plan, gaps):
+        t_next += gap
+        while time.perf_counter() < t_next:
+            pass
+        S.submit(gi, b.edge_id, b.new_cap)
+    S.drain()
+    st = S.stats()
+    S.close()
+    for G in Gs:
+        G.close()
+    return {"offered_rate_per_s": rate_per_s, "requests": st["completed"],
+            "batches_per_s": round(st["completed"] / max(st["makespan_s"], 1e-9), 1),
+            "p50_ms": round(st["p50_us"] / 1000, 3), "p99_ms": round(st["p99_us"] / 1000, 3),
+            "max_inflight": st["max_inflight"], "captured_graphs": st["captured_graphs"],
+            "failed": st["failed"]}
+
+
 def workload_config(args, g) -> dict:
     return {"workload": f"RMAT scale {SCALE} (n={g.n}, m={g.m}, a=0.57 b=0.19 c=0.19), caps U[1,1000], "
                         f"mixed batches of {args.batch} edges (+/-U[1,500])",
             "n": g.n, "m": g.m, "batch_edges": args.batch, "seed": SEED,
+            "kernel_cycles": args.kc, "policy": args.policy,
             "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -203,6 +259,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-sizes", action="store_true", help="skip the per-size dynamic/static comparison")
     ap.add_argument("--cpu-sample", type=int, default=3, help="batches in the CPU-oracle sample")
+    ap.add_argument("--kc", type=int, default=4, help="KERNELCYCLES of the repair (0 = average degree)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--policy", default="fixed", choices=["fixed", "plain", "learned"],
+                    help="batch policy: fixed repair, the plain rule, or the trained network")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -227,9 +287,16 @@ def main():
 
     g = gen.rmat(scale=SCALE, seed=SEED + 1000 * rank)
     cap = g.cap.copy()
-    G = MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t)
+    G = MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t, kernel_cycles=args.kc)
     G.solve()
     flow0 = G.flow_value()
+    if args.policy != "fixed":
+        from paper_2511_05895_gb300 import MF_POLICY_LEARNED, MF_POLICY_PLAIN
+        from paper_2511_05895_gb300.policy import load_default_params
+        if args.policy == "plain":
+            G.set_policy(MF_POLICY_PLAIN)
+        else:
+            G.set_policy(MF_POLICY_LEARNED, load_default_params())
 
     host_cap = cap.copy()
     batches = make_batches(host_cap, args.batch, args.warmup + args.steps, 0)
@@ -346,6 +413,11 @@ def main():
                "sample": f"{args.cpu_sample} recomputes from scratch (FIFO push-relabel, 1 thread) "
                          f"of the RMAT-20 graph after {args.batch}-edge batches"}
 
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = {"graphs": "RMAT-16, RMAT-18, grid 1024^2, bipartite 2^18+2^18 (4M unit edges)",
+                   "runs": [serving_measurement(r, 4.0) for r in (100.0, 1000.0)]}
+
     if dist:
         dist.destroy_process_group()
     if rank != 0:
@@ -381,6 +453,7 @@ def main():
         "clocks": clk,
         "cpu_baseline": cpu,
         "checks": {"flow_initial": flow0, "flow_final": flow_after, "certified": certified},
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
 

@@ -51,6 +51,17 @@ extern "C" {
                                 flow (the static recompute of Sec. 6.1) instead
                                 of the dynamic repair                            */
 
+/* ---- batch policies (mf_set_policy) ----------------------------------------
+ * FIXED    always the dynamic repair with the graph's KERNELCYCLES (default)
+ * PLAIN    dynamic repair when the batch holds at most 1 % of the edges,
+ *          else a static recompute; KERNELCYCLES = average degree (Sec. 6.1)
+ * LEARNED  the policy network (mf_mlp_*) chooses repair or recompute and
+ *          KERNELCYCLES from 12 batch features; it falls back to PLAIN on
+ *          any non-finite or out-of-range input */
+#define MF_POLICY_FIXED   0
+#define MF_POLICY_PLAIN   1
+#define MF_POLICY_LEARNED 2
+
 /* ---- processing modes (Sec. 5.2 / 5.3) ---------------------------------- */
 #define MF_MODE_DATA_DRIVEN 0  /* worklist of active vertices (Sec. 5.3)         */
 
@@ -102,7 +113,9 @@ typedef struct mf_options {
  *  barriers     grid barriers passed
  *  bfs_bottom_up_levels  BFS levels run bottom-up (direction-optimising)
  *  pr_rounds    PushRelabel activation rounds (vertices made active by a push
- *               are processed in the next round of the same iteration) */
+ *               are processed in the next round of the same iteration)
+ *  policy_*     last policy decision: kind 0 = repair, 1 = recompute; the
+ *               KERNELCYCLES chosen; 1 if the learned policy fell back */
 typedef struct mf_stats {
     int64_t flow;
     int64_t iterations;
@@ -131,6 +144,10 @@ typedef struct mf_stats {
     int64_t barriers;
     int64_t bfs_bottom_up_levels;
     int64_t pr_rounds;
+    int32_t policy_kind;
+    int32_t policy_kernel_cycles;
+    int32_t policy_fallback;
+    int32_t reserved1;
     int32_t status;
     int32_t kernel_cycles;
     int32_t grid_blocks;
@@ -185,6 +202,33 @@ int mf_solve(mf_graph *g, void *stream);
 int mf_apply_updates(mf_graph *g, int64_t k, const int32_t *edge_id, const int32_t *new_cap,
                      int32_t flags, void *stream);
 
+/* mf_apply_updates for a batch whose size lives in device memory (*k_dev,
+ * int32, at most k_max) with device arrays edge_id / new_cap: nothing in the
+ * call depends on host values, so it can be captured in a CUDA graph and
+ * replayed for every batch (the batch-sequence stamps are kept on the
+ * device).  Size the staging first with one call outside the capture (or a
+ * call of mf_apply_updates with k >= k_max).  Flags: MF_DELTA,
+ * MF_RECOMPUTE. */
+int mf_apply_updates_dev(mf_graph *g, const int32_t *k_dev, int64_t k_max, const int32_t *edge_id,
+                         const int32_t *new_cap, int32_t flags, void *stream);
+
+/* Enqueue on `stream` the copy of the last solve/repair's status and value
+ * into result[0..1] (host memory, preferably pinned): result[0] low 32 bits =
+ * status bits (1 rejected batch, 2 iteration cap, 4 device wait limit,
+ * 8 wall-clock limit; 0 = success), result[1] = flow value.  Does not wait. */
+int mf_flow_value_async(mf_graph *g, int64_t *result, void *stream);
+
+/* Wait for the graph's work, then make `stream` (NULL = legacy default
+ * stream) the stream that later synchronising calls wait on.  Call it before
+ * destroying a stream the graph last ran on. */
+int mf_set_stream(mf_graph *g, void *stream);
+
+/* Device memory the graph holds (bytes). */
+int mf_device_bytes(const mf_graph *g, int64_t *bytes);
+
+/* CTAs of the graph's persistent kernel (options.grid_blocks after clamping). */
+int mf_grid_blocks(const mf_graph *g, int32_t *blocks);
+
 /* Wait for the graph's work and report the status of the last solve/repair:
  * MF_OK, MF_EINVAL (rejected batch, reported once), MF_ETIMEOUT. */
 int mf_sync(mf_graph *g);
@@ -230,7 +274,7 @@ void mf_destroy(mf_graph *g);
  * another framework which owns all device memory through its own pool, or a
  * service path where allocations are forbidden after start-up -- and so
  * cannot use mf_create.  Instead of allocating, it works in one static
- * device array of 12,943,872 bytes (about 12.3 MiB) that every GPU which
+ * device array of 13,353,472 bytes (about 12.7 MiB) that every GPU which
  * loads this library holds until the process exits.
  *   n, arcs        vertices (2 .. 131072) and Bi-CSR arcs (0 .. 2097152);
  *                  larger graphs are rejected with MF_EINVAL
@@ -255,6 +299,130 @@ int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const in
                            const int32_t *rev, const int32_t *cap, int32_t s, int32_t t,
                            int32_t kernel_cycles, int32_t *r, int64_t *excess, int32_t *height,
                            int64_t *flow, void *stream);
+
+/* Choose how mf_apply_updates handles batches (MF_POLICY_*).  params: host
+ * array of the network (mf_mlp_sizes' n_total floats, layout in
+ * csrc/mf_mlp.cuh), required the first time LEARNED is set, copied; NULL
+ * keeps the loaded one.  MF_RECOMPUTE in a call's flags still forces a
+ * static recompute.  Synchronises when params is given. */
+int mf_set_policy(mf_graph *g, int32_t mode, const float *params);
+
+/* The 12 policy features of a batch for this graph (what the network sees):
+ * log2 n, log2 m, log2(1+k), k/m, share of increments, share of edges out of
+ * s or into t, log2(1 + sum |change|), log2(1 + last flow value), average
+ * Bi-CSR degree, log2(1 + largest degree), loop iterations of the last
+ * solve/repair, share of vertices its BFS reached per iteration.  Batch as in
+ * mf_apply_updates (flags MF_DEVICE_PTRS, MF_DELTA); features: host [12].
+ * Changes nothing.  Synchronises. */
+int mf_policy_features(mf_graph *g, int64_t k, const int32_t *edge_id, const int32_t *new_cap,
+                       int32_t flags, float *features);
+
+/* ---- the policy network (device arrays, float32, stream-ordered) -------
+ * Sizes: inputs 12, outputs 2, trained parameters, all parameters (with the
+ * input normalisation mu[12], sd[12] at the end). */
+int mf_mlp_sizes(int32_t *n_in, int32_t *n_out, int32_t *n_trained, int32_t *n_total);
+
+/* Bytes of the caller-provided workspace for mini-batches of `batch`. */
+int64_t mf_mlp_workspace_bytes(int32_t batch);
+
+/* Y[n x 2] = network(X[n x 12]); P: n_total parameters. */
+int mf_mlp_forward(const float *P, const float *X, int32_t n, float *Y, void *stream);
+
+/* Gradient (grad [n_trained]) and value (loss [1]) over all n samples of the
+ * mean loss BCE(y0, t0) + wkc * (y1 - t1)^2 / 2.  workspace:
+ * mf_mlp_workspace_bytes(n). */
+int mf_mlp_grad(const float *P, const float *X, const float *T0, const float *T1, int32_t n, float wkc,
+                float *grad, float *loss, void *workspace, void *stream);
+
+/* `steps` Adam steps (lr; betas 0.9, 0.999) on mini-batches of `batch`
+ * consecutive samples taken cyclically from X/T0/T1 (shuffle beforehand).
+ * M, V: Adam moments [n_trained] (zero before the first step); step0: steps
+ * taken before (for the bias correction).  loss_hist [steps] or NULL receives
+ * each mini-batch loss.  workspace: mf_mlp_workspace_bytes(batch). */
+int mf_mlp_train(float *P, float *M, float *V, const float *X, const float *T0, const float *T1, int32_t n,
+                 int32_t steps, int32_t batch, float lr, float wkc, int32_t step0, float *loss_hist,
+                 void *workspace, void *stream);
+
+/* ---- serving several resident graphs (continuous batching) --------------
+ * A server owns a scheduler thread.  Graphs (created, policy set and solved
+ * beforehand; each with its own grid size, mf_options.grid_blocks) are added
+ * to it; batches are submitted from host arrays and complete asynchronously.
+ * A request is admitted when its graph has no repair in flight, the CTAs of
+ * all repairs in flight stay within sm_slots (so that their persistent grids
+ * are co-resident and overlap), and their device staging fits the HBM budget
+ * left after the resident graphs; requests that do not fit wait while later
+ * ones for other graphs may start.  Each graph's repair is captured once in
+ * a CUDA graph and replayed (use_cuda_graphs; if capture fails the server
+ * launches directly and reports fewer captured graphs).  A graph belongs to
+ * the server once added: call nothing else on it until mf_server_destroy. */
+typedef struct mf_server mf_server;
+typedef struct mf_server_options {
+    int64_t hbm_budget_bytes;   /* 0 = the device's total memory                  */
+    int32_t sm_slots;           /* CTAs of all repairs in flight; 0 = SM count    */
+    int32_t use_cuda_graphs;    /* 1 (default) = replay captured repairs          */
+} mf_server_options;
+typedef struct mf_server_stats {
+    int64_t submitted, completed, failed;
+    int32_t max_inflight;       /* most repairs in flight at once                 */
+    int32_t graphs, captured_graphs;
+    int32_t reserved;
+    double p50_us, p99_us, mean_us;  /* submit-to-completion latency             */
+    double makespan_s;          /* first submit to last completion                */
+} mf_server_stats;
+
+int mf_server_options_default(mf_server_options *opt);
+int mf_server_create(const mf_server_options *opt, mf_server **out);
+/* Add a solved graph; max_batch bounds its batches.  MF_ENOMEM if it does not
+ * fit the HBM budget, MF_EINVAL if its grid exceeds sm_slots.  *index
+ * receives the graph's number for mf_server_submit.  Synchronises. */
+int mf_server_add_graph(mf_server *s, mf_graph *g, int64_t max_batch, int32_t *index);
+/* Queue a batch (host arrays, copied) for graph `graph`; flags MF_DELTA,
+ * MF_RECOMPUTE.  *ticket identifies the request. */
+int mf_server_submit(mf_server *s, int32_t graph, int64_t k, const int32_t *edge_id, const int32_t *new_cap,
+                     int32_t flags, int64_t *ticket);
+/* *done = 1 once the request completed; then *flow, *code (MF_OK, MF_EINVAL,
+ * MF_ETIMEOUT, MF_ECUDA) and *latency_us (submit to completion) are set. */
+int mf_server_poll(mf_server *s, int64_t ticket, int32_t *done, int64_t *flow, int32_t *code,
+                   double *latency_us);
+/* Wait until every submitted request completed. */
+int mf_server_drain(mf_server *s);
+int mf_server_stats_get(mf_server *s, mf_server_stats *out);
+/* Forget the latencies and counts of completed requests. */
+void mf_server_reset_stats(mf_server *s);
+/* Wait for all requests, stop the thread, free the server's resources (the
+ * graphs stay; destroy them afterwards). */
+void mf_server_destroy(mf_server *s);
+
+/* Tracing: one record per grid barrier of the solve/repair kernel.
+ *   phase  MF_PHASE_*; mode: BFS 0 top-down frontier, 1 top-down items of
+ *          high-degree vertices, 2 bottom-up groups, 3 bottom-up items; hub
+ *          cycles 0 set-up, 1 lowest-neighbour scan, 3 pushes
+ *   iter   loop iteration (-1 before the loop), step: BFS level, activation
+ *          round or hub cycle, count: frontier size, list size or items
+ *   ns     device time since the previous barrier (globaltimer of CTA 0) */
+#define MF_PHASE_BATCH          0  /* batch, capacity apply, clamp, re-saturation */
+#define MF_PHASE_HEIGHT_INIT    1
+#define MF_PHASE_BFS            2
+#define MF_PHASE_PUSH_RELABEL   3  /* activation rounds, one warp per vertex        */
+#define MF_PHASE_HUB            4  /* cooperative cycles of high-degree vertices    */
+#define MF_PHASE_REMOVE_INVALID 5
+typedef struct mf_trace_rec {
+    int16_t phase;
+    int16_t mode;
+    int32_t iter;
+    int32_t step;
+    int32_t count;
+    int64_t ns;
+} mf_trace_rec;
+
+/* Keep the records of each following solve/repair in a device buffer of
+ * `capacity` records (0 turns tracing off and frees the buffer).  Records past
+ * the capacity are counted but dropped.  Synchronises. */
+int mf_trace_enable(mf_graph *g, int32_t capacity);
+
+/* Copy up to max_records records of the last solve/repair to `out` (host);
+ * *count receives how many the launch produced.  Synchronises. */
+int mf_trace_read(mf_graph *g, mf_trace_rec *out, int32_t max_records, int32_t *count);
 
 /* Static string naming an error code. */
 const char *mf_strerror(int code);

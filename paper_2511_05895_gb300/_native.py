@@ -15,6 +15,7 @@ from . import _build
 
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_ENOTSOLVED, MF_ETIMEOUT = range(6)
 MF_HOST_PTRS, MF_DEVICE_PTRS, MF_DELTA, MF_RECOMPUTE = 0x0, 0x1, 0x2, 0x4
+MF_POLICY_FIXED, MF_POLICY_PLAIN, MF_POLICY_LEARNED = 0, 1, 2
 
 ERROR_NAMES = {MF_EINVAL: "MF_EINVAL", MF_ENOMEM: "MF_ENOMEM", MF_ECUDA: "MF_ECUDA",
                MF_ENOTSOLVED: "MF_ENOTSOLVED", MF_ETIMEOUT: "MF_ETIMEOUT"}
@@ -35,7 +36,9 @@ class Stats(ctypes.Structure):
         "flow", "iterations", "bfs_levels", "bfs_vertices", "bfs_arcs", "worklist", "pr_arcs",
         "pushes", "relabels", "ri_arcs", "ri_moves", "batch", "clamped", "resat_arcs", "n", "m",
         "arcs", "t_batch_ns", "t_reset_ns", "t_bfs_ns", "t_pr_ns", "t_hub_ns", "t_ri_ns",
-        "hub_cycles", "barriers", "bfs_bottom_up_levels", "pr_rounds")] + [(f, ctypes.c_int32) for f in ("status", "kernel_cycles", "grid_blocks",
+        "hub_cycles", "barriers", "bfs_bottom_up_levels", "pr_rounds")] + [
+        (f, ctypes.c_int32) for f in ("policy_kind", "policy_kernel_cycles", "policy_fallback",
+                                      "reserved1")] + [(f, ctypes.c_int32) for f in ("status", "kernel_cycles", "grid_blocks",
                                                    "block_threads")]
 
     def as_dict(self):
@@ -46,7 +49,21 @@ class Stats(ctypes.Structure):
 EXPORTED = ["mf_options_default", "mf_create", "mf_cap_limit", "mf_solve", "mf_apply_updates",
             "mf_sync", "mf_flow_value", "mf_min_cut", "mf_stats_get", "mf_sizes",
             "mf_export_graph", "mf_export_state", "mf_import_state", "mf_destroy",
-            "mf_strerror", "mf_version", "mf_last_error", "mf_bicsr_host", "mf_solve_bicsr_noalloc"]
+            "mf_strerror", "mf_version", "mf_last_error", "mf_bicsr_host", "mf_solve_bicsr_noalloc",
+            "mf_trace_enable", "mf_trace_read", "mf_set_policy", "mf_policy_features",
+            "mf_mlp_sizes", "mf_mlp_workspace_bytes", "mf_mlp_forward", "mf_mlp_grad", "mf_mlp_train",
+            "mf_apply_updates_dev", "mf_flow_value_async", "mf_set_stream", "mf_device_bytes", "mf_grid_blocks",
+            "mf_server_options_default", "mf_server_create", "mf_server_add_graph", "mf_server_submit",
+            "mf_server_poll", "mf_server_drain", "mf_server_stats_get", "mf_server_reset_stats",
+            "mf_server_destroy"]
+
+
+class TraceRec(ctypes.Structure):
+    _fields_ = [("phase", ctypes.c_int16), ("mode", ctypes.c_int16), ("iter", ctypes.c_int32),
+                ("step", ctypes.c_int32), ("count", ctypes.c_int32), ("ns", ctypes.c_int64)]
+
+
+PHASES = ["batch", "height_init", "bfs", "push_relabel", "hub", "remove_invalid"]
 
 
 class MFError(RuntimeError):
@@ -91,6 +108,30 @@ def lib(build_if_missing: bool = False):
         "mf_last_error": ([], ctypes.c_char_p),
         "mf_bicsr_host": ([i32, i64, P, P, P, i32, i32, P, P, P, P, P, P, P], ctypes.c_int),
         "mf_solve_bicsr_noalloc": ([i32, i64, P, P, P, P, i32, i32, i32, P, P, P, P, P], ctypes.c_int),
+        "mf_trace_enable": ([P, i32], ctypes.c_int),
+        "mf_trace_read": ([P, P, i32, P], ctypes.c_int),
+        "mf_set_policy": ([P, i32, P], ctypes.c_int),
+        "mf_policy_features": ([P, i64, P, P, i32, P], ctypes.c_int),
+        "mf_mlp_sizes": ([P, P, P, P], ctypes.c_int),
+        "mf_mlp_workspace_bytes": ([i32], i64),
+        "mf_mlp_forward": ([P, P, i32, P, P], ctypes.c_int),
+        "mf_mlp_grad": ([P, P, P, P, i32, ctypes.c_float, P, P, P, P], ctypes.c_int),
+        "mf_mlp_train": ([P, P, P, P, P, P, i32, i32, i32, ctypes.c_float, ctypes.c_float, i32, P, P, P],
+                         ctypes.c_int),
+        "mf_apply_updates_dev": ([P, P, i64, P, P, i32, P], ctypes.c_int),
+        "mf_flow_value_async": ([P, P, P], ctypes.c_int),
+        "mf_set_stream": ([P, P], ctypes.c_int),
+        "mf_device_bytes": ([P, P], ctypes.c_int),
+        "mf_grid_blocks": ([P, P], ctypes.c_int),
+        "mf_server_options_default": ([P], ctypes.c_int),
+        "mf_server_create": ([P, P], ctypes.c_int),
+        "mf_server_add_graph": ([P, P, i64, P], ctypes.c_int),
+        "mf_server_submit": ([P, i32, i64, P, P, i32, P], ctypes.c_int),
+        "mf_server_poll": ([P, i64, P, P, P, P], ctypes.c_int),
+        "mf_server_drain": ([P], ctypes.c_int),
+        "mf_server_stats_get": ([P, P], ctypes.c_int),
+        "mf_server_reset_stats": ([P], None),
+        "mf_server_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -260,6 +301,33 @@ class MaxFlowGraph:
         _check(lib().mf_stats_get(self._h, ctypes.byref(s)), "mf_stats_get")
         return s.as_dict()
 
+    def trace_enable(self, capacity=4096):
+        _check(lib().mf_trace_enable(self._h, int(capacity)), "mf_trace_enable")
+
+    def trace(self, max_records=4096):
+        """Records of the last solve/repair: a list of dicts (phase name, mode,
+        iter, step, count, ns)."""
+        buf = (TraceRec * max_records)()
+        cnt = ctypes.c_int32(0)
+        _check(lib().mf_trace_read(self._h, buf, max_records, ctypes.byref(cnt)), "mf_trace_read")
+        return [dict(phase=PHASES[r.phase], mode=r.mode, iter=r.iter, step=r.step, count=r.count, ns=r.ns)
+                for r in buf[:min(cnt.value, max_records)]]
+
+    def set_policy(self, mode, params=None):
+        """mode: MF_POLICY_FIXED / _PLAIN / _LEARNED; params: float32 network
+        parameters (numpy, mf_mlp_sizes' n_total) for the learned policy."""
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().mf_set_policy(self._h, int(mode), None if p is None else _np_ptr(p)), "mf_set_policy")
+
+    def policy_features(self, edge_id, new_cap, *, delta=False):
+        ip, f1, k1 = _array_arg(edge_id, np.int32)
+        cp, f2, k2 = _array_arg(new_cap, np.int32)
+        k = int(k1.shape[0]) if hasattr(k1, "shape") else len(k1)
+        out = np.zeros(12, np.float32)
+        _check(lib().mf_policy_features(self._h, k, ip, cp, f1 | (MF_DELTA if delta else 0), _np_ptr(out)),
+               "mf_policy_features")
+        return out
+
     def cap_limit(self) -> int:
         v = ctypes.c_int32(0)
         _check(lib().mf_cap_limit(self._h, ctypes.byref(v)), "mf_cap_limit")
@@ -295,3 +363,82 @@ class MaxFlowGraph:
         h = np.ascontiguousarray(h, np.int32)
         _check(lib().mf_import_state(self._h, _np_ptr(r), _np_ptr(e), _np_ptr(h), MF_HOST_PTRS),
                "mf_import_state")
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("sm_slots", ctypes.c_int32),
+                ("use_cuda_graphs", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("max_inflight", ctypes.c_int32), ("graphs", ctypes.c_int32),
+                ("captured_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("makespan_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class Server:
+    """Continuous-batching server over several resident graphs (mf_server_*).
+
+    Graphs are added once solved; afterwards only the server drives them."""
+
+    def __init__(self, hbm_budget_bytes=0, sm_slots=0, use_cuda_graphs=True):
+        L = lib()
+        o = ServerOptions()
+        L.mf_server_options_default(ctypes.byref(o))
+        o.hbm_budget_bytes = int(hbm_budget_bytes)
+        o.sm_slots = int(sm_slots)
+        o.use_cuda_graphs = 1 if use_cuda_graphs else 0
+        h = ctypes.c_void_p()
+        _check(L.mf_server_create(ctypes.byref(o), ctypes.byref(h)), "mf_server_create")
+        self._h = h
+        self._graphs = []
+
+    def add_graph(self, G, max_batch):
+        idx = ctypes.c_int32(-1)
+        _check(lib().mf_server_add_graph(self._h, G._h, int(max_batch), ctypes.byref(idx)), "mf_server_add_graph")
+        self._graphs.append(G)
+        return idx.value
+
+    def submit(self, graph, edge_id, new_cap, *, delta=False, recompute=False):
+        ids = np.ascontiguousarray(edge_id, np.int32)
+        caps = np.ascontiguousarray(new_cap, np.int32)
+        t = ctypes.c_int64(0)
+        flags = (MF_DELTA if delta else 0) | (MF_RECOMPUTE if recompute else 0)
+        _check(lib().mf_server_submit(self._h, int(graph), ids.shape[0], _np_ptr(ids), _np_ptr(caps), flags,
+                                      ctypes.byref(t)), "mf_server_submit")
+        return t.value
+
+    def poll(self, ticket):
+        d, c = ctypes.c_int32(0), ctypes.c_int32(0)
+        f = ctypes.c_int64(0)
+        lat = ctypes.c_double(0)
+        _check(lib().mf_server_poll(self._h, int(ticket), ctypes.byref(d), ctypes.byref(f), ctypes.byref(c),
+                                    ctypes.byref(lat)), "mf_server_poll")
+        return bool(d.value), f.value, c.value, lat.value
+
+    def drain(self):
+        _check(lib().mf_server_drain(self._h), "mf_server_drain")
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib().mf_server_stats_get(self._h, ctypes.byref(s)), "mf_server_stats_get")
+        return s.as_dict()
+
+    def reset_stats(self):
+        lib().mf_server_reset_stats(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mf_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

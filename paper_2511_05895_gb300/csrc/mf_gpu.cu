@@ -36,6 +36,7 @@
 
 #include "mf.h"
 #include "mf_internal.h"
+#include "mf_mlp.cuh"
 
 namespace mf {
 
@@ -50,10 +51,12 @@ constexpr int ST_WAIT = 4;     // a grid-barrier wait reached its time limit
 constexpr int ST_TIME = 8;     // the kernel ran past its wall-clock limit
 constexpr int ST_STICKY = ST_ITERS | ST_WAIT | ST_TIME;
 
-enum JobKind { JOB_SOLVE = 0, JOB_REPAIR = 1, JOB_RECOMPUTE = 2 };
+enum JobKind { JOB_SOLVE = 0, JOB_REPAIR = 1, JOB_RECOMPUTE = 2, JOB_AUTO = 3 };
 
-// PushRelabel activation rounds per loop iteration (see k_solve).
+// PushRelabel activation rounds per loop iteration, and the fewest
+// cooperative cycles the high-degree vertices get per iteration (see k_solve).
 constexpr int kMaxRounds = 16;
+constexpr int kMinHubCycles = 4;
 
 constexpr int S_COUNT_MAX = 24;
 
@@ -75,16 +78,22 @@ struct Ctl {
     int rlcnt;            // (z) relabel list size
     int rtk[3];           // (z) activation-round tickets, rotating by round
     unsigned stamp_base;  // first activation stamp of the next launch (kept across launches)
+    unsigned bseq;        // sequence number of the last batch (duplicate-id stamps)
     int wcnt;             // (z) active worklist size (vertices of degree <= kHubDeg)
     int hcnt;             // (z) active hub list size (degree > kHubDeg)
     int hccnt;            // (z) hub work items
     int hub_act[2];       // (z) hubs still active in the current hub cycle
+    int hlc[2];           // (z) live hub items for the next cycle, double-buffered
     int pad0;
     long long dacc[2];    // (z) sum of deficits at the last height init
     long long iters;
     unsigned long long t_start;  // globaltimer at kernel entry
+    int pol_kind;         // policy decision for the next JOB_AUTO launch
+    int pol_kc;
+    int pol_fallback;     // 1 if the learned policy fell back to the plain rule
+    float feat[12];       // features of the last batch the policy kernel saw
     int abort_loop;       // (z) set by thread 0 when the wall-clock limit passed
-    int pad1;
+    int trace_n;          // trace records written by the current launch
     long long st[S_COUNT_MAX];  // statistics, see enum Stat
 };
 
@@ -97,6 +106,13 @@ enum Stat {
     S_COUNT
 };
 static_assert(S_COUNT <= S_COUNT_MAX, "statistics array too small");
+
+// One trace record per grid barrier of k_solve (see mf_trace_read in mf.h).
+struct TraceRec {
+    short phase, mode;
+    int iter, step, count;
+    long long ns;
+};
 
 struct DevGraph {
     int n, s, t, m;
@@ -111,8 +127,12 @@ struct DevGraph {
     int *hl, *hmode;          // active hubs; per-hub cycle state
     int *hnit, *hdone;        // per-hub work items, and items finished in the cycle
     int2 *hcl;                // hub work items (hub index, first arc)
+    int2 *hlv0, *hlv1;        // items of the hubs still active, per cycle (double buffer)
+    unsigned *hikey;          // lowest residual-neighbour height per item of the current cycle
     unsigned long long *hkey; // per-hub lowest (height, arc) key
     long long *hrem;          // per-hub excess left to push in the current cycle
+    TraceRec *trace;          // per-barrier trace records, or null
+    int trace_cap;
     unsigned *astamp;         // per-vertex stamp of the last activation list joined
     unsigned *rstamp;         // per-vertex stamp of the last relabel list joined
     int *rl;                  // vertices relabelled in the current loop iteration
@@ -121,7 +141,7 @@ struct DevGraph {
 
 struct Job {
     int kind, k, flags, kc;
-    unsigned seq;
+    const int *k_dev;    // if set, the batch size is read from device memory
     long long max_iters;
     unsigned long long time_limit_ns;
     const int *ids, *caps;
@@ -235,6 +255,61 @@ struct ArcRoundBfs {
     int ra[kIlp], w[kIlp];
 };
 
+// Warp-aggregated append of the lanes' flagged values of kIlp slots: one
+// atomicAdd for the whole warp and all slots.  All 32 lanes call.
+__device__ __forceinline__ void warp_append_n(const bool (&pred)[kIlp], const int (&val)[kIlp], int *cnt, int *buf) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    unsigned m[kIlp];
+    int tot = 0;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        m[j] = __ballot_sync(kFull, pred[j]);
+        tot += __popc(m[j]);
+    }
+    if (tot == 0) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(cnt, tot);
+    base = __shfl_sync(kFull, base, 0);
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        if (pred[j]) buf[base + __popc(m[j] & below)] = val[j];
+        base += __popc(m[j]);
+    }
+}
+
+// bfs_discovered for kIlp slots per lane at once: the loads of all slots are
+// issued together and each list gets one reservation per warp.
+__device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (&disc)[kIlp], const int (&v)[kIlp],
+                                                 int *ncnt, int *NF, long long *asum, Counters &K) {
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) any |= disc[j];
+    if (!__any_sync(kFull, any)) return;
+    warp_append_n(disc, v, ncnt, NF);
+    int deg[kIlp];
+    long long ev[kIlp];
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        deg[j] = disc[j] ? __ldg(&G.row[v[j] + 1]) - __ldg(&G.row[v[j]]) : 0;
+        ev[j] = disc[j] ? lcg(&G.e[v[j]]) : 0;
+    }
+    long long ds = 0;
+    bool small[kIlp], hub[kIlp];
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        ds += deg[j];
+        K.bfs_verts += disc[j];
+        const bool act = disc[j] && ev[j] > 0;
+        hub[j] = act && deg[j] > kHubDeg;
+        small[j] = act && !hub[j];
+    }
+    ds = warp_sum(ds);
+    if ((threadIdx.x & 31) == 0 && ds) add_ll(asum, ds);
+    warp_append_n(small, v, &G.ctl->wcnt, G.wl);
+    warp_append_n(hub, v, &G.ctl->hcnt, G.hl);
+}
+
 // Bookkeeping of a vertex v reached at the next level (disc): it joins the
 // next frontier, its degree counts towards that frontier's arc total, and
 // with positive excess it is active: worklist (degree <= kHubDeg) or hub
@@ -280,8 +355,7 @@ __device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kI
     for (int j = 0; j < kIlp; ++j) hv[j] = (rin[j] > 0 && v[j] != G.s) ? lcg(&G.h[v[j]]) : -1;
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) disc[j] = hv[j] == n && atomicCAS(&G.h[v[j]], n, L + 1) == n;
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) bfs_discovered(G, disc[j], v[j], ncnt, NF, asum, K);
+    bfs_discovered_n(G, disc, v, ncnt, NF, asum, K);
 }
 
 // Expand up to 32 frontier vertices (one per lane, degree deg starting at
@@ -395,6 +469,7 @@ __device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item,
         const int a1 = min(item.y + kChunk, __ldg(&G.row[v + 1]));
         bool hit = false;
         for (int a0 = item.y; a0 < a1 && !hit; a0 += 32 * kIlp) {
+            if (a0 != item.y && __shfl_sync(kFull, lane == 0 ? lcg(&G.h[v]) : 0, 0) != G.n) break;
             ArcRoundBfs R;
 #pragma unroll
             for (int j = 0; j < kIlp; ++j) {
@@ -508,11 +583,89 @@ __device__ __forceinline__ unsigned long long round_min_key(const ArcRound &R, i
 // second pass over the arcs; otherwise it relabels u to h^ + 1.  A vertex
 // without residual arcs gets height n.  Only u's warp lowers r(u, .) and e(u);
 // other warps only raise them, so every amount pushed is available.
+// Still active after its steps: u takes part in the next round as well.
+__device__ __forceinline__ void requeue_if_active(const DevGraph &G, int u, const ActList &AL) {
+    if ((threadIdx.x & 31) == 0) {
+        const int hu = lcg(&G.h[u]);
+        if (hu < G.n && lcg(&G.e[u]) > 0 && atomicExch(&G.astamp[u], AL.stamp) != AL.stamp)
+            AL.list[atomicAdd(AL.cnt, 1)] = u;
+    }
+    __syncwarp();
+}
+
+// push_relabel_warp for a vertex whose arcs fit in one round (<= 32 kIlp):
+// the round loaded for the lowest-neighbour scan also serves the pushes (the
+// heights are the ones read once for the step, and u's own residuals can only
+// have grown since).
+__device__ __forceinline__ void push_relabel_small(const DevGraph &G, int u, int beg, int end, int kc,
+                                                   const ActList &AL, Counters &K) {
+    const int lane = threadIdx.x & 31;
+    const int n = G.n;
+    for (int c = 0; c < kc; ++c) {
+        int hu = 0;
+        long long eu = 0;
+        if (lane == 0) {
+            hu = lcg(&G.h[u]);
+            eu = lcg(&G.e[u]);
+        }
+        hu = __shfl_sync(kFull, hu, 0);
+        eu = __shfl_sync(kFull, eu, 0);
+        if (hu >= n || eu <= 0) break;
+        ArcRound R;
+        load_round(G, beg, end, R);
+        K.pr_arcs += round_arcs(beg, end);
+        const unsigned long long best = warp_min(round_min_key(R, beg, beg));
+        if (best == ~0ull) {
+            if (lane == 0) {
+                G.h[u] = n;
+                ++K.relabel;
+                note_relabel(G, u, AL.rstamp);
+            }
+            break;
+        }
+        const int hh = (int)(best >> 32);
+        if (hu <= hh) {
+            if (lane == 0) {
+                G.h[u] = hh + 1;
+                ++K.relabel;
+                note_relabel(G, u, AL.rstamp);
+            }
+            __syncwarp();
+            continue;
+        }
+        long long rem = eu, sent = 0;
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            const int ra = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
+            const long long incl = warp_incl_scan(ra);
+            long long d = rem - (incl - ra);
+            d = d < 0 ? 0 : (d > ra ? ra : d);
+            long long old = 0;
+            if (d > 0) {
+                old = push_arc(G, beg + 32 * j + lane, R.v[j], (int)d);
+                sent += d;
+                ++K.push;
+            }
+            note_activation(G, d > 0, R.v[j], old, d, AL);
+            const long long tot = __shfl_sync(kFull, incl, 31);
+            rem -= tot < rem ? tot : rem;
+        }
+        sent = warp_sum(sent);
+        if (lane == 0 && sent) add_ll(&G.e[u], -sent);
+        __syncwarp();
+    }
+    requeue_if_active(G, u, AL);
+}
+
 __device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int kc, const ActList &AL,
                                                   Counters &K) {
     const int lane = threadIdx.x & 31;
     const int n = G.n;
     const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
+    if (end - beg <= 32 * kIlp) {
+        push_relabel_small(G, u, beg, end, kc, AL, K);
+        return;
+    }
     for (int c = 0; c < kc; ++c) {
         int hu = 0;
         long long eu = 0;
@@ -576,6 +729,7 @@ __device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int 
         if (lane == 0 && sent) add_ll(&G.e[u], -sent);
         __syncwarp();
     }
+    requeue_if_active(G, u, AL);
 }
 
 // Algorithm 3 over the arcs [a0, a1) of vertex u (height hu) by one warp:
@@ -611,17 +765,26 @@ __device__ __forceinline__ void remove_invalid_warp(const DevGraph &G, int u, Co
 
 // ------------------------------------------------------------ the kernel --
 // Grid barrier inside k_solve; CTA 0's thread 0 charges the time since the
-// previous barrier to a phase bucket of the statistics.
-#define MF_SYNC(bucket)                                                       \
+// previous barrier to a phase bucket of the statistics and, when tracing is
+// on, appends a record (phase, loop iteration, step, mode, count, time).
+#define MF_SYNC_T(bucket, step, mode, aux)                                    \
     do {                                                                      \
         if (!grid_sync(C)) return;                                            \
         if (gtid == 0) {                                                      \
             const unsigned long long now_ = gtimer();                         \
-            C->st[bucket] += (long long)(now_ - tprev);                       \
+            const long long dt_ = (long long)(now_ - tprev);                  \
+            C->st[bucket] += dt_;                                             \
             C->st[S_BARRIERS] += 1;                                           \
+            if (G.trace) {                                                    \
+                const int k_ = C->trace_n++;                                  \
+                if (k_ < G.trace_cap)                                         \
+                    G.trace[k_] = TraceRec{(short)(bucket), (short)(mode),    \
+                                           (int)it, (int)(step), (int)(aux), dt_}; \
+            }                                                                 \
             tprev = now_;                                                     \
         }                                                                     \
     } while (0)
+#define MF_SYNC(bucket) MF_SYNC_T(bucket, -1, 0, -1)
 
 __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     Ctl *C = G.ctl;
@@ -633,20 +796,31 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     const int n = G.n, s = G.s, t = G.t;
     Counters K;
     unsigned long long tprev = gtimer();
+    long long it = -1;   // loop iteration (-1 before the loop, for trace records)
 
     // A sticky error (iteration cap, barrier wait) invalidates the state
     // until the next mf_solve, which clears it before launching.
     if (__ldcg(&C->status) & ST_STICKY) return;
     const unsigned stamp_base = __ldcg(&C->stamp_base) + 1u;
+    // JOB_AUTO: the policy kernel launched just before chose repair or
+    // recompute and KERNELCYCLES
+    int kind = J.kind, kc = J.kc;
+    if (kind == JOB_AUTO) {
+        kind = lcg(&C->pol_kind);
+        kc = lcg(&C->pol_kc);
+    }
+    const int kb = J.k_dev ? lcg(J.k_dev) : J.k;          // batch entries
+    const unsigned seq = __ldcg(&C->bseq) + 1u;           // this batch's stamp
     if (gtid == 0) {
         for (int i = 0; i < S_COUNT; ++i) C->st[i] = 0;
-        C->st[S_BATCH] = J.kind == JOB_SOLVE ? 0 : J.k;
+        C->st[S_BATCH] = kind == JOB_SOLVE ? 0 : kb;
         C->t_start = gtimer();
+        C->trace_n = 0;
     }
 
     // ---- batch: validate, then apply (Algorithm 5) ----------------------
-    if (J.kind != JOB_SOLVE) {
-        for (long long i = gtid; i < J.k; i += gthreads) {
+    if (kind != JOB_SOLVE) {
+        for (long long i = gtid; i < kb; i += gthreads) {
             const int eid = J.ids[i];
             bool bad = eid < 0 || eid >= G.m;
             int nc = 0;
@@ -658,7 +832,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 }
                 if (v < 0 || v > G.cap_limit) bad = true;
                 else nc = (int)v;
-                if (atomicExch(&G.stamp[eid], J.seq) == J.seq) bad = true;  // duplicate id
+                if (atomicExch(&G.stamp[eid], seq) == seq) bad = true;  // duplicate id
             }
             J.newc[i] = nc;
             if (bad) atomicOr(&C->batch_err, 1);
@@ -669,11 +843,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             if (gtid == 0) {
                 atomicOr(&C->status, ST_EINVAL);
                 C->batch_err = 0;
+                C->bseq = seq;
             }
             return;
         }
         // c_f(u,v) += c'(u,v) - c(u,v)  (Alg. 5, lines 1-3)
-        for (long long i = gtid; i < J.k; i += gthreads) {
+        for (long long i = gtid; i < kb; i += gthreads) {
             const int eid = J.ids[i];
             const int nc = lcg(&J.newc[i]);
             const int d = nc - lcg(&G.cap_edge[eid]);
@@ -682,18 +857,18 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             const int a = __ldg(&G.arc_of_edge[eid]);
             if (a >= 0 && d != 0) {
                 atomicAdd(&G.cap[a], d);
-                if (J.kind == JOB_REPAIR) {
+                if (kind == JOB_REPAIR) {
                     atomicAdd(&G.r[a], d);
                     atomicAdd(&G.rr[__ldg(&G.rev[a])], d);
                 }
             }
         }
         MF_SYNC(S_T_BATCH);
-        if (J.kind == JOB_REPAIR) {
+        if (kind == JOB_REPAIR) {
             // flow above the new capacity goes back: the tail keeps it as
             // excess, the head becomes deficient (Alg. 5, lines 4-11; the
             // excess update is the exact incremental form of Alg. 4 line 2).
-            for (long long i = gtid; i < J.k; i += gthreads) {
+            for (long long i = gtid; i < kb; i += gthreads) {
                 if (lcg(&J.dlt[i]) >= 0) continue;
                 const int a = __ldg(&G.arc_of_edge[J.ids[i]]);
                 if (a < 0) continue;
@@ -714,7 +889,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     }
 
     // ---- zero flow (Algorithm 1, first two loops) ------------------------
-    if (J.kind != JOB_REPAIR) {
+    if (kind != JOB_REPAIR) {
         for (long long a = gtid; a < G.A; a += gthreads) {
             G.r[a] = lcg(&G.cap[a]);
             G.rr[a] = lcg(&G.cap[__ldg(&G.rev[a])]);
@@ -746,7 +921,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     }
 
     // ---- device loop (Algorithm 4 while-loop) ----------------------------
-    long long it = 0;
+    it = 0;
     for (;; ++it) {
         const int par = (int)(it & 1);
         // height init: t and deficient vertices are sinks (height 0), all
@@ -764,6 +939,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             C->hcnt = 0;
             C->hccnt = 0;
             C->hub_act[0] = C->hub_act[1] = 0;
+            C->hlc[0] = C->hlc[1] = 0;
             C->dacc[par ^ 1] = 0;
             if (gtimer() - C->t_start > J.time_limit_ns) C->abort_loop = 1;
         }
@@ -786,7 +962,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             if (lane == 0 && dsum) add_ll(&C->dacc[par], dsum);
             if (lane == 0 && rdeg) add_ll(&C->asum[0], rdeg);
         }
-        MF_SYNC(S_T_RESET);
+        MF_SYNC_T(S_T_RESET, 0, 0, lcg(&C->qcnt[0]));
 
         // backward BFS from the sinks over residual arcs (global relabel),
         // level-synchronous and direction-optimising: top-down from the
@@ -848,7 +1024,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     bfs_expand_warp(G, beg, deg, L, ncnt, NF, asum, K);
                 }
             }
-            MF_SYNC(S_T_BFS);
+            MF_SYNC_T(S_T_BFS, L, bottom_up ? 2 : 0, cur);
             const int nch = lcg(ccnt);
             if (nch > 0) {
                 for (;;) {
@@ -873,7 +1049,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         bfs_visit_n(G, a, ok, L, ncnt, NF, asum, K);
                     }
                 }
-                MF_SYNC(S_T_BFS);
+                MF_SYNC_T(S_T_BFS, L, bottom_up ? 3 : 1, nch);
             }
             ++L;
         }
@@ -922,15 +1098,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 pos = __shfl_sync(kFull, pos, 0);
                 for (int c = lane; c < nc; c += 32) G.hcl[pos + c] = make_int2(i, beg + c * kPrChunk);
             }
-            MF_SYNC(S_T_HUB);
+            MF_SYNC_T(S_T_HUB, -1, 0, nh);
             nhc = lcg(&C->hccnt);
-            for (int c = 0; c < J.kc; ++c) {
+            const int hub_cycles = kc > kMinHubCycles ? kc : kMinHubCycles;
+            for (int c = 0; c < hub_cycles; ++c) {
                 if (gtid == 0) C->st[S_HUB_CYCLES] += 1;
                 // H1: lowest residual neighbour of every unfinished hub; the
                 // warp that completes a hub's last item takes the hub's
                 // decision (push at the lowest height, relabel, or finish)
-                for (int w = gwarp; w < nhc; w += nwarps) {
-                    const int2 item = lcg(&G.hcl[w]);
+                // the cycle's items: all hub items in cycle 0, afterwards the
+                // items of the hubs still active after the previous cycle
+                const int2 *items = c == 0 ? G.hcl : ((c - 1) & 1 ? G.hlv1 : G.hlv0);
+                const int nitems = c == 0 ? nhc : lcg(&C->hlc[(c - 1) & 1]);
+                for (int w = gwarp; w < nitems; w += nwarps) {
+                    const int2 item = lcg(&items[w]);
                     const int i = item.x;
                     if (lcg(&G.hmode[i]) < 0) continue;
                     const int u = lcg(&G.hl[i]);
@@ -945,7 +1126,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         best = k < best ? k : best;
                     }
                     best = warp_min(best);
+                    int decided = -2;   // -2: not the deciding warp; else the hub's mode
                     if (lane == 0) {
+                        G.hikey[w] = (unsigned)(best >> 32);   // lowest height in this item
                         if (best != ~0ull) atomicMin(&G.hkey[i], best);
                         __threadfence();
                         if (atomicAdd(&G.hdone[i], 1) == lcg(&G.hnit[i]) - 1) {
@@ -975,19 +1158,34 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             }
                             G.hmode[i] = mode;
                             if (mode >= 0) atomicAdd(&C->hub_act[c & 1], 1);
+                            decided = mode;
                         }
                     }
+                    // a hub that stays active takes all its items into the
+                    // next cycle's list, written by the warp that decided it
+                    decided = __shfl_sync(kFull, decided, 0);
+                    if (decided >= 0) {
+                        const int nit = lcg(&G.hnit[i]);
+                        int pos = 0;
+                        if (lane == 0) pos = atomicAdd(&C->hlc[c & 1], nit);
+                        pos = __shfl_sync(kFull, pos, 0);
+                        int2 *next_items = c & 1 ? G.hlv1 : G.hlv0;
+                        for (int q = lane; q < nit; q += 32) next_items[pos + q] = make_int2(i, beg + q * kPrChunk);
+                    }
                 }
-                MF_SYNC(S_T_HUB);
+                MF_SYNC_T(S_T_HUB, c, 1, nitems);
                 // hub_act[(c+1)&1] was last read by the exit test of cycle c-1,
                 // which every thread has passed once it is past the H1 barrier
                 if (gtid == 0) C->hub_act[(c + 1) & 1] = 0;
                 // H3: pushes along the lowest arcs; each warp reserves its share
                 // of the hub's excess with one atomic
-                for (int w = gwarp; w < nhc; w += nwarps) {
-                    const int2 item = lcg(&G.hcl[w]);
+                // hlc[(c+1)&1] counted the list of cycle c-1, read before H1
+                if (gtid == 0) C->hlc[(c + 1) & 1] = 0;
+                for (int w = gwarp; w < nitems; w += nwarps) {
+                    const int2 item = lcg(&items[w]);
                     const int mode = lcg(&G.hmode[item.x]);
                     if (mode <= 0) continue;
+                    if (lcg(reinterpret_cast<const int *>(&G.hikey[w])) != mode - 1) continue;  // no arc at h^ here
                     const int hh = mode - 1;
                     const int u = lcg(&G.hl[item.x]);
                     const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
@@ -1027,7 +1225,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     sent = warp_sum(sent);
                     if (lane == 0 && sent) add_ll(&G.e[u], -sent);
                 }
-                MF_SYNC(S_T_HUB);
+                MF_SYNC_T(S_T_HUB, c, 3, lcg(&C->hub_act[c & 1]));
                 if (lcg(&C->hub_act[c & 1]) == 0) break;
             }
         }
@@ -1048,9 +1246,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     if (lane == 0) i = atomicAdd(&C->rtk[rd % 3], 1);
                     i = __shfl_sync(kFull, i, 0);
                     if (i >= cnt) break;
-                    push_relabel_warp(G, lcg(&list[i]), J.kc, AL, K);
+                    push_relabel_warp(G, lcg(&list[i]), kc, AL, K);
                 }
-                MF_SYNC(S_T_PRW);
+                MF_SYNC_T(S_T_PRW, rd, 0, cnt);
                 cnt = lcg(AL.cnt);
                 list = nlist;
                 if (cnt == 0 || rd + 1 >= kMaxRounds) break;
@@ -1068,7 +1266,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             const long long moved = warp_sum(remove_invalid_range(G, hu, item.y, a1, K));
             if (lane == 0 && moved) add_ll(&G.e[u], -moved);
         }
-        MF_SYNC(S_T_RI);
+        MF_SYNC_T(S_T_RI, 0, 0, nrl);
     }
 
     // ---- result and statistics -------------------------------------------
@@ -1083,7 +1281,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         C->acnt[0] = C->acnt[1] = C->acnt[2] = 0;
         C->rtk[0] = C->rtk[1] = C->rtk[2] = 0;
         C->stamp_base = stamp_base + (unsigned)(it + 1) * (kMaxRounds + 1);
+        if (kind != JOB_SOLVE) C->bseq = seq;
         C->hub_act[0] = C->hub_act[1] = 0;
+        C->hlc[0] = C->hlc[1] = 0;
         C->dacc[0] = C->dacc[1] = 0;
         C->batch_err = 0;
         C->abort_loop = 0;
@@ -1094,6 +1294,114 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     for (int i = 0; i < 9; ++i) {
         const long long v = warp_sum(vals[i]);
         if (lane == 0 && v) add_ll(&C->st[idx[i]], v);
+    }
+}
+
+// ------------------------------------------------------------- policy --
+struct PolicyJob {
+    int k, flags, mode, kc_plain, max_deg;
+    const int *k_dev;      // if set, the batch size is read from device memory
+    const int *ids, *caps;
+    const float *params;   // network parameters (mf_mlp.cuh), or null
+};
+
+// Features of a batch and the policy decision for the k_solve launch that
+// follows (JOB_AUTO).  One CTA of 256 threads: block reductions over the batch
+// entries, then the 12 features, then the plain rule (dynamic repair when the
+// batch holds at most 1 % of the edges, KERNELCYCLES = average degree) or the
+// network, with the plain rule as fallback on any non-finite or out-of-range
+// input (|z| > 8).  Entries with bad ids are skipped here; k_solve rejects
+// the batch.
+__global__ void __launch_bounds__(256) k_policy(DevGraph G, PolicyJob PJ) {
+    Ctl *C = G.ctl;
+    if (PJ.k_dev) PJ.k = lcg(PJ.k_dev);
+    __shared__ float red[3][256];
+    __shared__ float x[mlp::kIn], z[mlp::kIn], h1[mlp::kH1], h2[mlp::kH2], y[mlp::kOut];
+    __shared__ int fb;
+    float inc = 0.f, touch = 0.f, sumd = 0.f;
+    for (int i = threadIdx.x; i < PJ.k; i += blockDim.x) {
+        const int id = PJ.ids[i];
+        if (id < 0 || id >= G.m) continue;
+        const long long old = lcg(&G.cap_edge[id]);
+        long long nc = PJ.caps[i];
+        if (PJ.flags & MF_DELTA) nc = old + nc < 0 ? 0 : old + nc;
+        inc += nc > old ? 1.f : 0.f;
+        sumd += (float)(nc > old ? nc - old : old - nc);
+        const int a = __ldg(&G.arc_of_edge[id]);
+        if (a >= 0 && (__ldg(&G.head[a]) == G.t || __ldg(&G.head[__ldg(&G.rev[a])]) == G.s)) touch += 1.f;
+    }
+    red[0][threadIdx.x] = inc;
+    red[1][threadIdx.x] = touch;
+    red[2][threadIdx.x] = sumd;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float n = (float)G.n, m = (float)(G.m > 0 ? G.m : 1), k = (float)PJ.k;
+        const float kk = k > 0.f ? k : 1.f;
+        const long long iters = lcg(&C->iters);
+        const long long reached = lcg(&C->st[S_BFS_VERTS]);
+        x[0] = log2f(n);
+        x[1] = log2f(m);
+        x[2] = log2f(1.f + k);
+        x[3] = k / m;
+        x[4] = red[0][0] / kk;
+        x[5] = red[1][0] / kk;
+        x[6] = log2f(1.f + red[2][0]);
+        const long long fl = lcg(&C->flow);
+        x[7] = log2f(1.f + (float)(fl < 0 ? -fl : fl));
+        x[8] = (float)G.A / n;
+        x[9] = log2f(1.f + (float)PJ.max_deg);
+        x[10] = (float)iters;
+        x[11] = (float)reached / ((float)(iters + 1) * n);
+        for (int j = 0; j < mlp::kIn; ++j) C->feat[j] = x[j];
+        fb = PJ.mode != MF_POLICY_LEARNED || PJ.params == nullptr;
+        if (!fb)
+            for (int j = 0; j < mlp::kIn; ++j) {
+                z[j] = (x[j] - PJ.params[mlp::oMu + j]) / PJ.params[mlp::oSd + j];
+                if (!isfinite(z[j]) || fabsf(z[j]) > 8.f) fb = 1;
+            }
+    }
+    __syncthreads();
+    if (!fb) {
+        const float *P = PJ.params;
+        if (threadIdx.x < mlp::kH1) {
+            float a = P[mlp::oB1 + threadIdx.x];
+            for (int j = 0; j < mlp::kIn; ++j) a += P[mlp::oW1 + threadIdx.x * mlp::kIn + j] * z[j];
+            h1[threadIdx.x] = a > 0.f ? a : 0.f;
+        }
+        __syncthreads();
+        if (threadIdx.x < mlp::kH2) {
+            float a = P[mlp::oB2 + threadIdx.x];
+            for (int j = 0; j < mlp::kH1; ++j) a += P[mlp::oW2 + threadIdx.x * mlp::kH1 + j] * h1[j];
+            h2[threadIdx.x] = a > 0.f ? a : 0.f;
+        }
+        __syncthreads();
+        if (threadIdx.x < mlp::kOut) {
+            float a = P[mlp::oB3 + threadIdx.x];
+            for (int j = 0; j < mlp::kH2; ++j) a += P[mlp::oW3 + threadIdx.x * mlp::kH2 + j] * h2[j];
+            y[threadIdx.x] = a;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int kind, kc;
+        bool fallback = fb != 0;
+        if (!fallback && !(isfinite(y[0]) && isfinite(y[1]))) fallback = true;
+        if (fallback) {
+            kind = (long long)PJ.k * 100 <= (long long)G.m ? JOB_REPAIR : JOB_RECOMPUTE;
+            kc = PJ.kc_plain;
+        } else {
+            kind = y[0] > 0.f ? JOB_REPAIR : JOB_RECOMPUTE;
+            const float l = fminf(fmaxf(rintf(y[1]), 0.f), 6.f);
+            kc = 1 << (int)l;
+        }
+        C->pol_kind = kind;
+        C->pol_kc = kc;
+        C->pol_fallback = (PJ.mode == MF_POLICY_LEARNED && fallback) ? 1 : 0;
     }
 }
 
@@ -1126,7 +1434,10 @@ struct NoAllocLayout {
     static constexpr size_t rstamp = astamp + align256(sizeof(unsigned) * kNoAllocMaxN);
     static constexpr size_t cb = rstamp + align256(sizeof(unsigned) * kNoAllocMaxN);
     static constexpr size_t hcl = cb + align256(sizeof(int2) * (kNoAllocMaxArcs / kChunk + kNoAllocMaxN));
-    static constexpr size_t hl = hcl + align256(sizeof(int2) * (kNoAllocMaxArcs / kPrChunk + kNoAllocMaxHubs));
+    static constexpr size_t hlv0 = hcl + align256(sizeof(int2) * (kNoAllocMaxArcs / kPrChunk + kNoAllocMaxHubs));
+    static constexpr size_t hlv1 = hlv0 + align256(sizeof(int2) * (kNoAllocMaxArcs / kPrChunk + kNoAllocMaxHubs));
+    static constexpr size_t hikey = hlv1 + align256(sizeof(int2) * (kNoAllocMaxArcs / kPrChunk + kNoAllocMaxHubs));
+    static constexpr size_t hl = hikey + align256(sizeof(unsigned) * (kNoAllocMaxArcs / kPrChunk + kNoAllocMaxHubs));
     static constexpr size_t hmode = hl + align256(sizeof(int) * kNoAllocMaxHubs);
     static constexpr size_t hnit = hmode + align256(sizeof(int) * kNoAllocMaxHubs);
     static constexpr size_t hdone = hnit + align256(sizeof(int) * kNoAllocMaxHubs);
@@ -1135,7 +1446,7 @@ struct NoAllocLayout {
     static constexpr size_t total = hrem + align256(sizeof(long long) * kNoAllocMaxHubs);
 };
 
-static_assert(NoAllocLayout::total == 12943872, "the header states the scratch size (12,943,872 bytes)");
+static_assert(NoAllocLayout::total == 13353472, "the header states the scratch size (13,353,472 bytes)");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NoAllocLayout::total];
 
 }  // namespace mf
@@ -1155,11 +1466,14 @@ struct mf_graph {
     mf_options opt{};
     DevGraph dg{};
     std::vector<void *> owned;
+    std::vector<size_t> owned_bytes;
     int *b_ids = nullptr, *b_caps = nullptr, *b_newc = nullptr, *b_dlt = nullptr;
     int64_t b_cap = 0;
     unsigned char *side_buf = nullptr;
-    unsigned seq = 0;
     bool solved = false;
+    int policy = MF_POLICY_FIXED;
+    float *params = nullptr;   // policy network parameters on the device
+    int max_deg = 0;
     cudaStream_t last = nullptr;
 };
 
@@ -1210,8 +1524,20 @@ void dfree(mf_graph *g, void *p) {
 template <class T>
 T *dnew(mf_graph *g, size_t count) {
     T *p = static_cast<T *>(dalloc(g, count * sizeof(T)));
-    if (p) g->owned.push_back(p);
+    if (p) {
+        g->owned.push_back(p);
+        g->owned_bytes.push_back(count * sizeof(T));
+    }
     return p;
+}
+
+void dforget(mf_graph *g, void *p) {
+    for (size_t i = 0; i < g->owned.size(); ++i)
+        if (g->owned[i] == p) {
+            g->owned.erase(g->owned.begin() + long(i));
+            g->owned_bytes.erase(g->owned_bytes.begin() + long(i));
+            return;
+        }
 }
 
 bool is_device_ptr(const void *p) {
@@ -1255,6 +1581,22 @@ int launch(mf_graph *g, const Job &job, cudaStream_t st) {
     return MF_OK;
 }
 
+int launch_policy(mf_graph *g, int64_t k, const int *ids, const int *caps, int flags, cudaStream_t st) {
+    PolicyJob pj{};
+    pj.k = int(k);
+    pj.flags = flags;
+    pj.mode = g->policy;
+    pj.kc_plain = g->kc;
+    pj.max_deg = g->max_deg;
+    pj.ids = ids;
+    pj.caps = caps;
+    pj.params = g->params;
+    k_policy<<<1, 256, 0, st>>>(g->dg, pj);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(MF_ECUDA, std::string("policy launch: ") + cudaGetErrorString(e));
+    return MF_OK;
+}
+
 int ensure_batch_capacity(mf_graph *g, int64_t k, cudaStream_t st) {
     if (k <= g->b_cap) return MF_OK;
     int64_t want = std::max<int64_t>(k, std::max<int64_t>(1024, g->b_cap * 2));
@@ -1264,7 +1606,7 @@ int ensure_batch_capacity(mf_graph *g, int64_t k, cudaStream_t st) {
     for (int *p : ptrs) {
         if (!p) continue;
         dfree(g, p);
-        g->owned.erase(std::remove(g->owned.begin(), g->owned.end(), (void *)p), g->owned.end());
+        dforget(g, p);
     }
     g->b_ids = dnew<int>(g, size_t(want));
     g->b_caps = dnew<int>(g, size_t(want));
@@ -1381,6 +1723,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
 
     g->n = n; g->m = m; g->A = H.arcs; g->s = s; g->t = t;
     g->cap_limit = H.cap_limit;
+    g->max_deg = H.max_deg;
     int64_t avg = (m + n / 2) / n;
     g->kc = g->opt.kernel_cycles > 0 ? g->opt.kernel_cycles : int(std::max<int64_t>(1, avg));
     g->max_iters = g->opt.max_iters > 0 ? g->opt.max_iters : 4LL * n + 1000;
@@ -1404,6 +1747,9 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     D.hnit = dnew<int>(g, NH);
     D.hdone = dnew<int>(g, NH);
     D.hcl = dnew<int2>(g, size_t(std::max<int64_t>(H.hub_chunk_items, 1)));
+    D.hlv0 = dnew<int2>(g, size_t(std::max<int64_t>(H.hub_chunk_items, 1)));
+    D.hlv1 = dnew<int2>(g, size_t(std::max<int64_t>(H.hub_chunk_items, 1)));
+    D.hikey = dnew<unsigned>(g, size_t(std::max<int64_t>(H.hub_chunk_items, 1)));
     D.astamp = dnew<unsigned>(g, N);
     D.rstamp = dnew<unsigned>(g, N);
     D.rl = dnew<int>(g, N);
@@ -1411,7 +1757,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     g->side_buf = dnew<unsigned char>(g, N);
     if (!row || !head || !rev || !aoe || !D.cap || !D.r || !D.rr || !D.h || !D.e || !D.cap_edge || !D.stamp ||
         !D.qb0 || !D.qb1 || !D.wl || !D.cb || !D.ctl || !g->side_buf || !D.hl || !D.hmode || !D.hkey ||
-        !D.hrem || !D.hnit || !D.hdone || !D.hcl || !D.astamp || !D.rstamp || !D.rl)
+        !D.hrem || !D.hnit || !D.hdone || !D.hcl || !D.hlv0 || !D.hlv1 || !D.hikey || !D.astamp || !D.rstamp || !D.rl)
         return fail(MF_ENOMEM, "device allocation failed");
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
@@ -1452,6 +1798,7 @@ int mf_solve(mf_graph *g, void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     MF_CUDA(cudaSetDevice(g->dev));
     MF_CUDA(cudaMemsetAsync(g->dg.ctl, 0, sizeof(Ctl), st));
+    MF_CUDA(cudaMemsetAsync(g->dg.stamp, 0, size_t(std::max<int64_t>(g->m, 1)) * 4, st));
     MF_CUDA(cudaMemsetAsync(g->dg.astamp, 0, size_t(g->n) * 4, st));
     MF_CUDA(cudaMemsetAsync(g->dg.rstamp, 0, size_t(g->n) * 4, st));
     Job j{};
@@ -1484,11 +1831,14 @@ int mf_apply_updates(mf_graph *g, int64_t k, const int32_t *edge_id, const int32
     }
     Job j{};
     j.kind = (flags & MF_RECOMPUTE) ? JOB_RECOMPUTE : JOB_REPAIR;
+    if (!(flags & MF_RECOMPUTE) && g->policy != MF_POLICY_FIXED) {
+        rc = launch_policy(g, k, ids, caps, flags, st);
+        if (rc) return rc;
+        j.kind = JOB_AUTO;
+    }
     j.k = int(k);
     j.flags = flags;
     j.kc = g->kc;
-    j.seq = ++g->seq;
-    if (g->seq == 0) j.seq = g->seq = 1;
     j.max_iters = g->max_iters;
     j.time_limit_ns = g->time_limit_ns;
     j.ids = ids;
@@ -1496,6 +1846,82 @@ int mf_apply_updates(mf_graph *g, int64_t k, const int32_t *edge_id, const int32
     j.newc = g->b_newc;
     j.dlt = g->b_dlt;
     return launch(g, j, st);
+}
+
+int mf_apply_updates_dev(mf_graph *g, const int32_t *k_dev, int64_t k_max, const int32_t *edge_id,
+                         const int32_t *new_cap, int32_t flags, void *stream) {
+    if (!g || !k_dev || !edge_id || !new_cap) return set_err(MF_EINVAL, "null argument");
+    if (!g->solved) return set_err(MF_ENOTSOLVED, "call mf_solve first");
+    if (k_max < 0 || k_max > g->m) return set_err(MF_EINVAL, "bad k_max");
+    if (flags & ~(MF_DELTA | MF_RECOMPUTE | MF_DEVICE_PTRS)) return set_err(MF_EINVAL, "unknown flags");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MF_CUDA(cudaSetDevice(g->dev));
+    if (g->b_cap < std::max<int64_t>(k_max, 1)) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        MF_CUDA(cudaStreamIsCapturing(st, &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            return set_err(MF_EINVAL, "batch staging must be sized (k_max) before stream capture");
+        int rc = ensure_batch_capacity(g, std::max<int64_t>(k_max, 1), st);
+        if (rc) return rc;
+    }
+    Job j{};
+    j.kind = (flags & MF_RECOMPUTE) ? JOB_RECOMPUTE : JOB_REPAIR;
+    if (!(flags & MF_RECOMPUTE) && g->policy != MF_POLICY_FIXED) {
+        PolicyJob pj{};
+        pj.k = 0;
+        pj.k_dev = k_dev;
+        pj.flags = flags & MF_DELTA;
+        pj.mode = g->policy;
+        pj.kc_plain = g->kc;
+        pj.max_deg = g->max_deg;
+        pj.ids = edge_id;
+        pj.caps = new_cap;
+        pj.params = g->params;
+        k_policy<<<1, 256, 0, st>>>(g->dg, pj);
+        MF_CUDA(cudaGetLastError());
+        j.kind = JOB_AUTO;
+    }
+    j.k = 0;
+    j.k_dev = k_dev;
+    j.flags = flags;
+    j.kc = g->kc;
+    j.max_iters = g->max_iters;
+    j.time_limit_ns = g->time_limit_ns;
+    j.ids = edge_id;
+    j.caps = new_cap;
+    j.newc = g->b_newc;
+    j.dlt = g->b_dlt;
+    return launch(g, j, st);
+}
+
+int mf_set_stream(mf_graph *g, void *stream) {
+    if (!g) return MF_EINVAL;
+    MF_CUDA(cudaSetDevice(g->dev));
+    if (g->last) MF_CUDA(cudaStreamSynchronize(g->last));
+    g->last = static_cast<cudaStream_t>(stream);
+    return MF_OK;
+}
+
+int mf_flow_value_async(mf_graph *g, int64_t *result, void *stream) {
+    if (!g || !result) return MF_EINVAL;
+    MF_CUDA(cudaSetDevice(g->dev));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    MF_CUDA(cudaMemcpyAsync(result, g->dg.ctl, 16, cudaMemcpyDeviceToHost, st));
+    return MF_OK;
+}
+
+int mf_device_bytes(const mf_graph *g, int64_t *bytes) {
+    if (!g || !bytes) return MF_EINVAL;
+    int64_t b = 0;
+    for (size_t x : g->owned_bytes) b += int64_t(x);
+    *bytes = b;
+    return MF_OK;
+}
+
+int mf_grid_blocks(const mf_graph *g, int32_t *blocks) {
+    if (!g || !blocks) return MF_EINVAL;
+    *blocks = g->grid;
+    return MF_OK;
 }
 
 int mf_sync(mf_graph *g) {
@@ -1565,6 +1991,9 @@ int mf_stats_get(mf_graph *g, mf_stats *out) {
     out->barriers = c.st[S_BARRIERS];
     out->bfs_bottom_up_levels = c.st[S_BU_LEVELS];
     out->pr_rounds = c.st[S_ROUNDS];
+    out->policy_kind = c.pol_kind == JOB_RECOMPUTE ? 1 : 0;
+    out->policy_kernel_cycles = c.pol_kc;
+    out->policy_fallback = c.pol_fallback;
     out->status = c.status;
     out->kernel_cycles = g->kc;
     out->grid_blocks = g->grid;
@@ -1621,6 +2050,9 @@ int mf_import_state(mf_graph *g, const int32_t *r, const int64_t *excess, const 
     for (int32_t v = 0; v < g->n; ++v)
         if (v != g->s && v != g->t && he[size_t(v)] < 0) flow += he[size_t(v)];
     MF_CUDA(cudaMemset(g->dg.ctl, 0, sizeof(Ctl)));
+    MF_CUDA(cudaMemset(g->dg.stamp, 0, size_t(std::max<int64_t>(g->m, 1)) * 4));
+    MF_CUDA(cudaMemset(g->dg.astamp, 0, size_t(g->n) * 4));
+    MF_CUDA(cudaMemset(g->dg.rstamp, 0, size_t(g->n) * 4));
     MF_CUDA(cudaMemcpy(&g->dg.ctl->flow, &flow, sizeof(flow), cudaMemcpyHostToDevice));
     MF_CUDA(cudaDeviceSynchronize());
     g->solved = true;
@@ -1634,6 +2066,92 @@ void mf_destroy(mf_graph *g) {
     cudaDeviceSynchronize();
     for (void *p : g->owned) dfree(g, p);
     delete g;
+}
+
+int mf_set_policy(mf_graph *g, int32_t mode, const float *params) {
+    if (!g || mode < MF_POLICY_FIXED || mode > MF_POLICY_LEARNED) return MF_EINVAL;
+    if (mode == MF_POLICY_LEARNED && !params && !g->params)
+        return set_err(MF_EINVAL, "the learned policy needs network parameters");
+    MF_CUDA(cudaSetDevice(g->dev));
+    if (params) {
+        if (!g->params) g->params = dnew<float>(g, mlp::kTotal);
+        if (!g->params) return set_err(MF_ENOMEM, "policy parameter allocation failed");
+        MF_CUDA(cudaStreamSynchronize(g->last));
+        MF_CUDA(cudaMemcpy(g->params, params, sizeof(float) * mlp::kTotal, cudaMemcpyHostToDevice));
+    }
+    g->policy = mode;
+    return MF_OK;
+}
+
+int mf_policy_features(mf_graph *g, int64_t k, const int32_t *edge_id, const int32_t *new_cap, int32_t flags,
+                       float *features) {
+    if (!g || !features || k < 0 || k > g->m || (k > 0 && (!edge_id || !new_cap))) return MF_EINVAL;
+    MF_CUDA(cudaSetDevice(g->dev));
+    cudaStream_t st = g->last;
+    int rc = ensure_batch_capacity(g, std::max<int64_t>(k, 1), st);
+    if (rc) return rc;
+    const int *ids = edge_id, *caps = new_cap;
+    if (!(flags & MF_DEVICE_PTRS) && k > 0) {
+        MF_CUDA(cudaMemcpyAsync(g->b_ids, edge_id, size_t(k) * 4, cudaMemcpyHostToDevice, st));
+        MF_CUDA(cudaMemcpyAsync(g->b_caps, new_cap, size_t(k) * 4, cudaMemcpyHostToDevice, st));
+        ids = g->b_ids;
+        caps = g->b_caps;
+    }
+    rc = launch_policy(g, k, ids, caps, flags & MF_DELTA, st);
+    if (rc) return rc;
+    Ctl c;
+    rc = read_ctl(g, &c);
+    if (rc) return rc;
+    for (int j = 0; j < mlp::kIn; ++j) features[j] = c.feat[j];
+    return MF_OK;
+}
+
+int mf_trace_enable(mf_graph *g, int32_t capacity) {
+    if (!g || capacity < 0) return MF_EINVAL;
+    MF_CUDA(cudaSetDevice(g->dev));
+    MF_CUDA(cudaStreamSynchronize(g->last));
+    if (g->dg.trace) {
+        dfree(g, g->dg.trace);
+        dforget(g, g->dg.trace);
+        g->dg.trace = nullptr;
+        g->dg.trace_cap = 0;
+    }
+    if (capacity == 0) return MF_OK;
+    g->dg.trace = dnew<TraceRec>(g, size_t(capacity));
+    if (!g->dg.trace) return set_err(MF_ENOMEM, "trace buffer allocation failed");
+    g->dg.trace_cap = capacity;
+    return MF_OK;
+}
+
+int mf_trace_read(mf_graph *g, mf_trace_rec *out, int32_t max_records, int32_t *count) {
+    if (!g || !count || max_records < 0 || (max_records > 0 && !out)) return MF_EINVAL;
+    Ctl c;
+    int rc = read_ctl(g, &c);
+    if (rc) return rc;
+    const int avail = std::min(c.trace_n, g->dg.trace_cap);
+    *count = c.trace_n;
+    const int k = std::min(avail, int(max_records));
+    if (k <= 0 || !g->dg.trace) return MF_OK;
+    std::vector<TraceRec> tmp(static_cast<size_t>(k));
+    MF_CUDA(cudaMemcpy(tmp.data(), g->dg.trace, size_t(k) * sizeof(TraceRec), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < k; ++i) {
+        int ph = MF_PHASE_BATCH;
+        switch (tmp[size_t(i)].phase) {
+            case S_T_RESET: ph = MF_PHASE_HEIGHT_INIT; break;
+            case S_T_BFS: ph = MF_PHASE_BFS; break;
+            case S_T_PRW: ph = MF_PHASE_PUSH_RELABEL; break;
+            case S_T_HUB: ph = MF_PHASE_HUB; break;
+            case S_T_RI: ph = MF_PHASE_REMOVE_INVALID; break;
+            default: ph = MF_PHASE_BATCH; break;
+        }
+        out[i].phase = int16_t(ph);
+        out[i].mode = tmp[size_t(i)].mode;
+        out[i].iter = tmp[size_t(i)].iter;
+        out[i].step = tmp[size_t(i)].step;
+        out[i].count = tmp[size_t(i)].count;
+        out[i].ns = tmp[size_t(i)].ns;
+    }
+    return MF_OK;
 }
 
 // Allocation-free static solve on a caller-provided Bi-CSR (see mf.h).
@@ -1684,6 +2202,9 @@ int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const in
     D.rstamp = reinterpret_cast<unsigned *>(b + Lo::rstamp);
     D.cb = reinterpret_cast<int2 *>(b + Lo::cb);
     D.hcl = reinterpret_cast<int2 *>(b + Lo::hcl);
+    D.hlv0 = reinterpret_cast<int2 *>(b + Lo::hlv0);
+    D.hlv1 = reinterpret_cast<int2 *>(b + Lo::hlv1);
+    D.hikey = reinterpret_cast<unsigned *>(b + Lo::hikey);
     D.hl = reinterpret_cast<int *>(b + Lo::hl);
     D.hmode = reinterpret_cast<int *>(b + Lo::hmode);
     D.hnit = reinterpret_cast<int *>(b + Lo::hnit);

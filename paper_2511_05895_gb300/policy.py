@@ -1,0 +1,281 @@
+"""The learned batch policy: logging, training and evaluation.
+
+The paper observes that the dynamic repair wins for small batches and a
+static recompute wins past a crossover (Sec. 6.5), and that KERNELCYCLES
+trades pushes against global relabels (Note 2 of Sec. 3).  A small network
+(csrc/mf_mlp.cuh) predicts both choices from 12 batch features
+(mf_policy_features); the library evaluates it on the device before each
+repair when the graph's policy is MF_POLICY_LEARNED, and falls back to the
+plain rule on unusual inputs.
+
+* ``collect``  runs the method itself on seeded workloads and logs, per
+  batch, the features and the device time of the dynamic repair at each
+  KERNELCYCLES value of ``KC_CHOICES`` and of a static recompute;
+* ``train``    fits the network with the library's own CUDA kernels
+  (mf_mlp_train: forward, backward and Adam on the GPU);
+* ``evaluate`` replays logged batches: total time of the decisions of the
+  learned policy against the plain rule (and the best possible choice).
+
+Every repair and recompute during collection is still an exact solve; the
+flow values of all instances are compared batch by batch.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _native
+from ._native import MaxFlowGraph, lib
+
+KC_CHOICES = (1, 2, 4, 8, 16)
+KC_STATIC = 4
+PARAMS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "policy_params.npy")
+N_IN = 12
+
+
+def sizes():
+    a, b, c, d = (ctypes.c_int32() for _ in range(4))
+    lib().mf_mlp_sizes(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d))
+    return a.value, b.value, c.value, d.value
+
+
+def load_default_params():
+    """The committed trained parameters, or None."""
+    return np.load(PARAMS_PATH).astype(np.float32) if os.path.exists(PARAMS_PATH) else None
+
+
+# ---------------------------------------------------------------- logging --
+def _time_apply(G, ids, caps, recompute=False):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    G.apply_updates(ids, caps, recompute=recompute)
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def collect_graph(g, batches, group, log):
+    """Run every batch of ``batches`` (iterable of workloads.generators.Batch,
+    applied cumulatively) through one graph instance per KC choice plus one
+    static-recompute instance; append rows to ``log`` (dict of lists)."""
+    import torch
+    inst = [MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=kc) for kc in KC_CHOICES]
+    stat = MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=KC_STATIC)
+    for G in inst + [stat]:
+        G.solve()
+    flows = {G.flow_value() for G in inst + [stat]}
+    assert len(flows) == 1, flows
+    observer = inst[KC_CHOICES.index(4)]
+    for b in batches:
+        ids = torch.from_numpy(b.edge_id).cuda()
+        caps = torch.from_numpy(b.new_cap).cuda()
+        feats = observer.policy_features(ids, caps)
+        t_dyn = [_time_apply(G, ids, caps) for G in inst]
+        t_st = _time_apply(stat, ids, caps, recompute=True)
+        flows = {G.flow_value() for G in inst + [stat]}
+        assert len(flows) == 1, flows                 # every choice is exact
+        log["X"].append(feats)
+        log["t_dyn"].append(t_dyn)
+        log["t_static"].append(t_st)
+        log["group"].append(group)
+        log["k"].append(len(b.edge_id))
+    for G in inst + [stat]:
+        G.close()
+
+
+def labels(t_dyn, t_static):
+    """Targets: T0 = 1 if the best dynamic repair beats the static recompute,
+    T1 = log2 of the best KERNELCYCLES for the repair."""
+    best = t_dyn.min(axis=1)
+    T0 = (best < t_static).astype(np.float32)
+    T1 = np.log2(np.asarray(KC_CHOICES, np.float32)[t_dyn.argmin(axis=1)])
+    return T0, T1
+
+
+# --------------------------------------------------------------- training --
+def train(X, T0, T1, steps=6000, batch=256, lr=2e-3, wkc=0.25, seed=0):
+    """Fit the network on the GPU with mf_mlp_train; returns float32 params."""
+    import torch
+    n_in, n_out, n_tr, n_tot = sizes()
+    X = np.asarray(X, np.float32)
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(X.shape[0])
+    X, T0, T1 = X[perm], np.asarray(T0, np.float32)[perm], np.asarray(T1, np.float32)[perm]
+    mu = X.mean(axis=0)
+    sd = X.std(axis=0)
+    sd[sd < 1e-3] = 1.0
+    P = np.zeros(n_tot, np.float32)
+    # He initialisation of the layers (the layout is that of csrc/mf_mlp.cuh)
+    o = 0
+    for (fan_out, fan_in), gain in (((64, 12), 2.0), ((64, 64), 2.0), ((2, 64), 1.0)):
+        P[o:o + fan_out * fan_in] = rng.normal(0, np.sqrt(gain / fan_in), fan_out * fan_in)
+        o += fan_out * fan_in + fan_out
+    P[n_tr:n_tr + n_in] = mu
+    P[n_tr + n_in:] = sd
+    dev = torch.device("cuda")
+    tP = torch.from_numpy(P).to(dev)
+    tM = torch.zeros(n_tr, device=dev)
+    tV = torch.zeros(n_tr, device=dev)
+    tX = torch.from_numpy(np.ascontiguousarray(X)).to(dev)
+    tT0 = torch.from_numpy(np.ascontiguousarray(T0)).to(dev)
+    tT1 = torch.from_numpy(np.ascontiguousarray(T1)).to(dev)
+    B = min(batch, X.shape[0])
+    ws = torch.empty(int(lib().mf_mlp_workspace_bytes(B)) // 4 + 1, device=dev)
+    hist = torch.zeros(steps, device=dev)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    rc = lib().mf_mlp_train(p(tP), p(tM), p(tV), p(tX), p(tT0), p(tT1), X.shape[0], steps, B, lr, wkc, 0,
+                            p(hist), p(ws), st)
+    if rc != 0:
+        raise _native.MFError(rc, "mf_mlp_train")
+    torch.cuda.synchronize()
+    return tP.cpu().numpy(), hist.cpu().numpy()
+
+
+def forward(P, X):
+    """Network outputs for X through mf_mlp_forward (GPU)."""
+    import torch
+    dev = torch.device("cuda")
+    tP = torch.from_numpy(np.ascontiguousarray(P, np.float32)).to(dev)
+    tX = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
+    tY = torch.zeros((tX.shape[0], 2), device=dev)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib().mf_mlp_forward(ctypes.c_void_p(tP.data_ptr()), ctypes.c_void_p(tX.data_ptr()), tX.shape[0],
+                              ctypes.c_void_p(tY.data_ptr()), st)
+    if rc != 0:
+        raise _native.MFError(rc, "mf_mlp_forward")
+    return tY.cpu().numpy()
+
+
+# ------------------------------------------------------------- evaluation --
+def _kc_index(kc):
+    kc = np.asarray(kc)
+    return np.abs(np.log2(kc)[:, None] - np.log2(np.asarray(KC_CHOICES))[None, :]).argmin(axis=1)
+
+
+def decide_plain(X):
+    """The plain rule: repair iff k <= 1 % of m; KERNELCYCLES = average degree
+    (feature 8 is the average Bi-CSR degree, about 2 m / n)."""
+    X = np.asarray(X)
+    repair = X[:, 3] <= 0.01
+    m, n = 2.0 ** X[:, 1], 2.0 ** X[:, 0]
+    kc = np.maximum(1, np.rint(m / n))
+    return repair, kc
+
+
+def decide_learned(P, X):
+    """Decisions of the device kernel (k_policy), from the same outputs."""
+    Y = forward(P, X)
+    repair = Y[:, 0] > 0
+    kc = 2.0 ** np.clip(np.rint(Y[:, 1]), 0, 6)
+    return repair, kc
+
+
+def cost(repair, kc, t_dyn, t_static):
+    idx = _kc_index(kc)
+    return np.where(repair, t_dyn[np.arange(len(idx)), idx], t_static)
+
+
+def evaluate(data, P):
+    X, t_dyn, t_st = data["X"], data["t_dyn"], data["t_static"]
+    rp, kp = decide_plain(X)
+    rl, kl = decide_learned(P, X)
+    best = np.minimum(t_dyn.min(axis=1), t_st)
+    return {"batches": int(X.shape[0]), "plain_ms": float(cost(rp, kp, t_dyn, t_st).sum()),
+            "learned_ms": float(cost(rl, kl, t_dyn, t_st).sum()), "best_ms": float(best.sum()),
+            "always_dynamic_default_kc_ms": float(cost(np.ones_like(rp), kp, t_dyn, t_st).sum())}
+
+
+# -------------------------------------------------------------------- CLI --
+def _specs():
+    """Seeded workloads of the logging run: (name, group, graph factory,
+    batch factory (cap, i, rng) -> Batch, number of batches)."""
+    from workloads import generators as gen
+
+    def mixed(lo, hi, kmin, kmax_frac):
+        def make(g, cap, i, rng):
+            k = int(np.exp(rng.uniform(np.log(kmin), np.log(max(kmin + 1, kmax_frac * g.m)))))
+            return gen.mixed_batch(cap, min(k, g.m), lo, hi, seed=int(rng.integers(1 << 30)), index=i)
+        return make
+
+    def rect(side_lo, side_hi):
+        def make(g, cap, i, rng):
+            return gen.grid_rect_batch(g, seed=int(rng.integers(1 << 30)), index=i, side_lo=side_lo,
+                                       side_hi=side_hi)
+        return make
+
+    out = []
+    for s in range(20):
+        out.append((f"random_s{s}", len(out), lambda s=s: gen.random_graph(seed=s), mixed(1, 50, 5, 0.5), 100))
+    for sc, seeds, nb in ((14, 8, 100), (16, 4, 80), (18, 2, 40), (20, 1, 30)):
+        for s in range(seeds):
+            out.append((f"rmat{sc}_s{s}", len(out), lambda sc=sc, s=s: gen.rmat(scale=sc, seed=100 + s),
+                        mixed(1, 500, 100, 0.08), nb))
+    for W, seeds, nb, lo, hi in ((512, 2, 40, 16, 128), (1024, 1, 30, 64, 512)):
+        for s in range(seeds):
+            out.append((f"grid{W}_s{s}", len(out), lambda W=W, s=s: gen.grid_segmentation(W, W, seed=200 + s),
+                        rect(lo, hi), nb))
+    return out
+
+
+def main(argv=None):
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    c = sub.add_parser("collect")
+    c.add_argument("--out", required=True)
+    c.add_argument("--limit", type=int, default=0, help="only the first N workloads")
+    t = sub.add_parser("train")
+    t.add_argument("--data", required=True)
+    t.add_argument("--out", default=PARAMS_PATH)
+    t.add_argument("--steps", type=int, default=6000)
+    e = sub.add_parser("eval")
+    e.add_argument("--data", required=True)
+    e.add_argument("--params", default=PARAMS_PATH)
+    args = ap.parse_args(argv)
+    if args.cmd == "collect":
+        log = {"X": [], "t_dyn": [], "t_static": [], "group": [], "k": []}
+        names = []
+        t0 = time.time()
+        specs = _specs()[: args.limit or None]
+        for name, group, make_graph, make_batch, nb in specs:
+            g = make_graph()
+            cap = g.cap.copy()
+            rng = np.random.default_rng(1000 + group)
+
+            def batches(g=g, cap=cap, rng=rng, make_batch=make_batch, nb=nb):
+                from workloads import generators as gen
+                for i in range(nb):
+                    b = make_batch(g, cap, i, rng)
+                    gen.apply_batch(cap, b)
+                    yield b
+            collect_graph(g, batches(), group, log)
+            names.append(name)
+            print(json.dumps({"workload": name, "rows": len(log["k"]), "s": round(time.time() - t0, 1)}), flush=True)
+        np.savez_compressed(args.out, X=np.asarray(log["X"], np.float32), t_dyn=np.asarray(log["t_dyn"], np.float32),
+                            t_static=np.asarray(log["t_static"], np.float32), group=np.asarray(log["group"], np.int32),
+                            k=np.asarray(log["k"], np.int64), names=np.asarray(names), kc=np.asarray(KC_CHOICES))
+    elif args.cmd == "train":
+        d = np.load(args.data)
+        train_rows = d["group"] % 4 != 3            # every 4th workload is held out
+        T0, T1 = labels(d["t_dyn"], d["t_static"])
+        P, hist = train(d["X"][train_rows], T0[train_rows], T1[train_rows], steps=args.steps)
+        np.save(args.out, P)
+        print(json.dumps({"train_rows": int(train_rows.sum()), "loss_first": float(hist[:50].mean()),
+                          "loss_last": float(hist[-50:].mean())}))
+    else:
+        d = np.load(args.data)
+        held = d["group"] % 4 == 3
+        P = np.load(args.params)
+        sub_d = {k: d[k][held] for k in ("X", "t_dyn", "t_static")}
+        print(json.dumps({"held_out": evaluate(sub_d, P), "all": evaluate({k: d[k] for k in sub_d}, P)}))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,150 @@
+"""The serving loop (mf_server_*): several resident graphs, continuous
+batching, CUDA-graph-captured repairs.
+
+Each graph's flow value after each of its batches is the same when the
+batches are served alone (one graph, direct calls) and when they are served
+in the mix through the server with the other graphs' batches overlapping on
+the device; both equal the CPU oracle (tolerance: exact, integer flows)."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import generators as gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2511_05895_gb300 as pkg
+    return pkg
+
+
+def workloads():
+    gs = [gen.random_graph(seed=51), gen.rmat(scale=12, seed=52), gen.rmat(scale=13, seed=53),
+          gen.grid_segmentation(96, 64, seed=54)]
+    seqs = []
+    for gi, g in enumerate(gs):
+        cap = g.cap.copy()
+        bs = []
+        for j in range(6):
+            if g.meta.get("kind") == "grid":
+                b = gen.grid_rect_batch(g, seed=54, index=j, side_lo=8, side_hi=40)
+            else:
+                b = gen.mixed_batch(cap, max(10, g.m // (200 if j % 2 else 20)), 1, 100, seed=gi, index=j)
+            gen.apply_batch(cap, b)
+            bs.append(b)
+        seqs.append(bs)
+    return gs, seqs
+
+
+def test_results_alone_equal_results_in_the_mix(mf):
+    gs, seqs = workloads()
+    # alone: direct calls, one graph at a time
+    alone = []
+    for g, bs in zip(gs, seqs):
+        G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t)
+        G.solve()
+        G.flow_value()
+        fl = []
+        for b in bs:
+            G.apply_updates(b.edge_id, b.new_cap)
+            fl.append(G.flow_value())
+        alone.append(fl)
+        G.close()
+    # oracle on the cumulative capacities
+    for g, bs, fl in zip(gs, seqs, alone):
+        cap = g.cap.copy()
+        for b, f in zip(bs, fl):
+            gen.apply_batch(cap, b)
+            assert f == oracle.maxflow_fifo(g.n, g.row_ptr, g.col, cap, g.s, g.t)
+    # in the mix: four graphs on grids of 38 CTAs, all batches queued at once
+    S = mf.Server(sm_slots=152)
+    Gs = []
+    for g, bs in zip(gs, seqs):
+        G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, grid_blocks=38)
+        G.solve()
+        G.flow_value()
+        Gs.append(G)
+        S.add_graph(G, max(len(b.edge_id) for b in bs))
+    rng = np.random.default_rng(0)
+    order = np.concatenate([np.full(len(bs), gi) for gi, bs in enumerate(seqs)])
+    rng.shuffle(order)
+    nxt = [0] * len(gs)
+    tickets = {}
+    for gi in order:
+        j = nxt[gi]
+        nxt[gi] += 1
+        b = seqs[gi][j]
+        tickets[(gi, j)] = S.submit(int(gi), b.edge_id, b.new_cap)
+    S.drain()
+    for (gi, j), t in tickets.items():
+        done, flow, code, lat = S.poll(t)
+        assert done and code == 0
+        assert flow == alone[gi][j], (gi, j)
+    st = S.stats()
+    assert st["completed"] == st["submitted"] == sum(len(b) for b in seqs)
+    assert st["failed"] == 0 and st["max_inflight"] >= 2
+    assert st["p99_us"] >= st["p50_us"] > 0
+    S.close()
+    for G in Gs:
+        G.close()
+
+
+def test_sm_slots_serialise_and_hbm_budget_admits(mf):
+    g1, g2 = gen.rmat(scale=11, seed=61), gen.random_graph(seed=62)
+    G1 = mf.MaxFlowGraph(g1.n, g1.row_ptr, g1.col, g1.cap, g1.s, g1.t, grid_blocks=38)
+    G2 = mf.MaxFlowGraph(g2.n, g2.row_ptr, g2.col, g2.cap, g2.s, g2.t, grid_blocks=38)
+    for G in (G1, G2):
+        G.solve()
+        G.flow_value()
+    # a budget that holds one graph only
+    import ctypes
+    b1, b2 = ctypes.c_int64(0), ctypes.c_int64(0)
+    mf.lib().mf_device_bytes(G1._h, ctypes.byref(b1))
+    mf.lib().mf_device_bytes(G2._h, ctypes.byref(b2))
+    staging = 4 * (4 + 2 * 4096)
+    assert b2.value > 4 * staging
+    S = mf.Server(hbm_budget_bytes=b1.value + 2 * staging, sm_slots=38)
+    S.add_graph(G1, 4096)
+    with pytest.raises(mf.MFError) as ei:
+        S.add_graph(G2, 4096)
+    assert ei.value.code == mf.MF_ENOMEM
+    cap = g1.cap.copy()
+    ts = []
+    for j in range(4):
+        b = gen.mixed_batch(cap, 300, 1, 100, seed=61, index=j)
+        gen.apply_batch(cap, b)
+        ts.append(S.submit(0, b.edge_id, b.new_cap))
+    S.drain()
+    assert S.poll(ts[-1])[1] == oracle.maxflow_fifo(g1.n, g1.row_ptr, g1.col, cap, g1.s, g1.t)
+    assert S.stats()["max_inflight"] == 1
+    S.close()
+    G1.close()
+    G2.close()
+
+
+def test_cuda_graph_capture_and_recompute_requests(mf):
+    g = gen.rmat(scale=12, seed=71)
+    G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, grid_blocks=76)
+    G.solve()
+    G.flow_value()
+    S = mf.Server()
+    S.add_graph(G, 2000)
+    st = S.stats()
+    cap = g.cap.copy()
+    out = []
+    for j in range(4):
+        b = gen.mixed_batch(cap, 500, 1, 100, seed=71, index=j)
+        gen.apply_batch(cap, b)
+        t = S.submit(0, b.edge_id, b.new_cap, recompute=(j == 2))
+        out.append((t, oracle.maxflow_fifo(g.n, g.row_ptr, g.col, cap, g.s, g.t)))
+    S.drain()
+    for t, want in out:
+        assert S.poll(t)[1] == want
+    print("captured graphs:", st["captured_graphs"])
+    assert st["captured_graphs"] in (0, 2)
+    S.close()
+    G.close()

@@ -279,3 +279,49 @@ def test_update_monotonicity_bounds():
     down = cap.copy()
     down[::7] = np.maximum(down[::7] - 5, 0)
     assert oracle.maxflow_fifo(g.n, g.row_ptr, g.col, down, g.s, g.t) <= f_old
+
+
+# ---- the policy network oracle -------------------------------------------
+from oracle import mlp as omlp  # noqa: E402
+
+
+def _mlp_case(seed, n=40):
+    rng = np.random.default_rng(seed)
+    P = omlp.init_params(rng, mu=rng.normal(0, 1, 12), sd=rng.uniform(0.5, 2.0, 12))
+    P[omlp.O_B1:omlp.O_W2] = rng.normal(0, 0.1, 64)   # biases away from 0 (ReLU kinks)
+    P[omlp.O_B2:omlp.O_W3] = rng.normal(0, 0.1, 64)
+    X = rng.normal(0, 1.5, (n, 12))
+    T0 = (rng.uniform(size=n) < 0.5).astype(np.float64)
+    T1 = rng.uniform(0, 5, n)
+    return P, X, T0, T1
+
+
+def test_mlp_gradient_matches_central_differences():
+    P, X, T0, T1 = _mlp_case(1)
+    L, g = omlp.loss_and_grad(P, X, T0, T1, 0.3)
+    assert abs(L - omlp.loss(P, X, T0, T1, 0.3)) < 1e-12
+    rng = np.random.default_rng(2)
+    idx = np.concatenate([rng.choice(omlp.N_TRAINED, 120, replace=False),
+                          np.arange(omlp.O_B3, omlp.N_TRAINED)])
+    h = 1e-6
+    for i in idx:
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        fd = (omlp.loss(Pp, X, T0, T1, 0.3) - omlp.loss(Pm, X, T0, T1, 0.3)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_mlp_closed_form_with_zero_output_weights():
+    """With W3 = 0 the outputs are the biases: the loss and the gradient of b3
+    have closed forms."""
+    P, X, T0, T1 = _mlp_case(3)
+    P[omlp.O_W3:omlp.O_B3] = 0.0
+    c0, c1 = 0.7, -1.2
+    P[omlp.O_B3:omlp.N_TRAINED] = [c0, c1]
+    L, g = omlp.loss_and_grad(P, X, T0, T1, 2.0)
+    want = np.log1p(np.exp(c0)) - T0.mean() * c0 + 0.5 * 2.0 * np.mean((c1 - T1) ** 2)
+    assert abs(L - want) < 1e-12
+    assert abs(g[omlp.O_B3] - (1 / (1 + np.exp(-c0)) - T0.mean())) < 1e-12
+    assert abs(g[omlp.O_B3 + 1] - 2.0 * np.mean(c1 - T1)) < 1e-12
+    assert np.all(g[:omlp.O_W3] == 0.0)          # nothing reaches the hidden layers

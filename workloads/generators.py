@@ -350,3 +350,20 @@ def grid_rect_batch(g: Graph, seed: int, index: int, side_lo: int = 64, side_hi:
 def apply_batch(cur_cap: np.ndarray, batch: Batch) -> None:
     """Write a batch's absolute capacities into the host copy of the caps."""
     cur_cap[batch.edge_id.astype(np.int64)] = batch.new_cap
+
+
+def bipartite(left: int = 1 << 20, right: int = 1 << 20, m: int = 16 << 20, seed: int = 0) -> Graph:
+    """Unit-capacity assignment graph: s -> every left vertex, m uniform
+    left -> right edges, every right vertex -> t (max flow = maximum
+    matching).  Vertices: left 0 .. L-1, right L .. L+R-1, s = L+R, t = L+R+1."""
+    st = Stream(seed, "bipartite")
+    L, R = left, right
+    s, t = L + R, L + R + 1
+    lu = st.integers(m, 0, L - 1)
+    rv = L + st.integers(m, 0, R - 1)
+    tails = np.concatenate([np.full(L, s, np.int64), lu, np.arange(L, L + R, dtype=np.int64)])
+    heads = np.concatenate([np.arange(L, dtype=np.int64), rv, np.full(R, t, np.int64)])
+    g = from_edges(L + R + 2, tails, heads, np.ones(tails.shape[0], np.int64), s, t,
+                   name=f"bipartite{L}x{R}_m{m}_seed{seed}")
+    g.meta.update(kind="bipartite", seed=seed)
+    return g
