@@ -64,6 +64,8 @@ extern "C" {
 
 /* ---- processing modes (Sec. 5.2 / 5.3) ---------------------------------- */
 #define MF_MODE_DATA_DRIVEN 0  /* worklist of active vertices (Sec. 5.3)         */
+#define MF_MODE_TOPOLOGY    1  /* the first push/relabel round of each iteration
+                                  visits every vertex id (Sec. 5.2)            */
 
 typedef struct mf_graph mf_graph;
 
@@ -71,7 +73,7 @@ typedef struct mf_graph mf_graph;
  *  kernel_cycles  KERNELCYCLES of Algorithm 2: push/relabel steps per active
  *                 vertex between two global relabels.  0 = max(1, round(m/n)),
  *                 the average degree used in Sec. 6.1.
- *  mode           MF_MODE_DATA_DRIVEN.
+ *  mode           MF_MODE_DATA_DRIVEN (default) or MF_MODE_TOPOLOGY.
  *  max_iters      cap on loop iterations (one BFS + PushRelabel +
  *                 RemoveInvalidEdges round) of one solve or repair; reaching
  *                 it reports MF_ETIMEOUT.  0 = 4 * n + 1000.

@@ -16,6 +16,7 @@ from . import _build
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_ENOTSOLVED, MF_ETIMEOUT = range(6)
 MF_HOST_PTRS, MF_DEVICE_PTRS, MF_DELTA, MF_RECOMPUTE = 0x0, 0x1, 0x2, 0x4
 MF_POLICY_FIXED, MF_POLICY_PLAIN, MF_POLICY_LEARNED = 0, 1, 2
+MF_MODE_DATA_DRIVEN, MF_MODE_TOPOLOGY = 0, 1
 
 ERROR_NAMES = {MF_EINVAL: "MF_EINVAL", MF_ENOMEM: "MF_ENOMEM", MF_ECUDA: "MF_ECUDA",
                MF_ENOTSOLVED: "MF_ENOTSOLVED", MF_ETIMEOUT: "MF_ETIMEOUT"}
@@ -214,7 +215,8 @@ class MaxFlowGraph:
     (CPU or CUDA); the stream defaults to torch's current stream."""
 
     def __init__(self, n, row_ptr, col, cap, s, t, *, kernel_cycles=0, max_iters=0,
-                 grid_blocks=0, time_limit_ms=0, torch_allocator=False, stream=None):
+                 grid_blocks=0, time_limit_ms=0, mode=MF_MODE_DATA_DRIVEN, torch_allocator=False,
+                 stream=None):
         L = lib()
         self._opt = Options()
         L.mf_options_default(ctypes.byref(self._opt))
@@ -222,6 +224,7 @@ class MaxFlowGraph:
         self._opt.max_iters = max_iters
         self._opt.grid_blocks = grid_blocks
         self._opt.time_limit_ms = time_limit_ms
+        self._opt.mode = mode
         self._keep = []
         if torch_allocator:
             torch = _torch()

@@ -140,7 +140,7 @@ struct DevGraph {
 };
 
 struct Job {
-    int kind, k, flags, kc;
+    int kind, k, flags, kc, mode;
     const int *k_dev;    // if set, the batch size is read from device memory
     long long max_iters;
     unsigned long long time_limit_ns;
@@ -1241,12 +1241,33 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     C->st[S_ROUNDS] += 1;
                     C->st[S_WL] += cnt;
                 }
-                for (;;) {
-                    int i = 0;
-                    if (lane == 0) i = atomicAdd(&C->rtk[rd % 3], 1);
-                    i = __shfl_sync(kFull, i, 0);
-                    if (i >= cnt) break;
-                    push_relabel_warp(G, lcg(&list[i]), kc, AL, K);
+                if (rd == 0 && J.mode == MF_MODE_TOPOLOGY) {
+                    // topology-driven (Sec. 5.2): every vertex id is visited;
+                    // each warp takes 32 ids and serves the active ones
+                    for (;;) {
+                        int grp = 0;
+                        if (lane == 0) grp = atomicAdd(&C->rtk[0], 1);
+                        const int base = __shfl_sync(kFull, grp, 0) * 32;
+                        if (base >= n) break;
+                        const int v = base + lane;
+                        bool act = false;
+                        if (v < n && v != s && v != t && __ldg(&G.row[v + 1]) - __ldg(&G.row[v]) <= kHubDeg)
+                            act = lcg(&G.h[v]) < n && lcg(&G.e[v]) > 0;
+                        unsigned mask = __ballot_sync(kFull, act);
+                        while (mask) {
+                            const int j = __ffs(mask) - 1;
+                            mask &= mask - 1u;
+                            push_relabel_warp(G, base + j, kc, AL, K);
+                        }
+                    }
+                } else {
+                    for (;;) {
+                        int i = 0;
+                        if (lane == 0) i = atomicAdd(&C->rtk[rd % 3], 1);
+                        i = __shfl_sync(kFull, i, 0);
+                        if (i >= cnt) break;
+                        push_relabel_warp(G, lcg(&list[i]), kc, AL, K);
+                    }
                 }
                 MF_SYNC_T(S_T_PRW, rd, 0, cnt);
                 cnt = lcg(AL.cnt);
@@ -1710,6 +1731,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
         return set_err(code, msg);
     };
     if ((g->opt.alloc == nullptr) != (g->opt.free == nullptr)) return fail(MF_EINVAL, "alloc and free must both be set");
+    if (g->opt.mode != MF_MODE_DATA_DRIVEN && g->opt.mode != MF_MODE_TOPOLOGY) return fail(MF_EINVAL, "unknown mode");
     if (cudaGetDevice(&g->dev) != cudaSuccess) return fail(MF_ECUDA, "no CUDA device");
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->dev);
@@ -1804,6 +1826,7 @@ int mf_solve(mf_graph *g, void *stream) {
     Job j{};
     j.kind = JOB_SOLVE;
     j.kc = g->kc;
+    j.mode = g->opt.mode;
     j.max_iters = g->max_iters;
     j.time_limit_ns = g->time_limit_ns;
     int rc = launch(g, j, st);
@@ -1839,6 +1862,7 @@ int mf_apply_updates(mf_graph *g, int64_t k, const int32_t *edge_id, const int32
     j.k = int(k);
     j.flags = flags;
     j.kc = g->kc;
+    j.mode = g->opt.mode;
     j.max_iters = g->max_iters;
     j.time_limit_ns = g->time_limit_ns;
     j.ids = ids;
@@ -1885,6 +1909,7 @@ int mf_apply_updates_dev(mf_graph *g, const int32_t *k_dev, int64_t k_max, const
     j.k_dev = k_dev;
     j.flags = flags;
     j.kc = g->kc;
+    j.mode = g->opt.mode;
     j.max_iters = g->max_iters;
     j.time_limit_ns = g->time_limit_ns;
     j.ids = edge_id;

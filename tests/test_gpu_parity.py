@@ -327,3 +327,11 @@ def test_trace_records(mf):
     G.trace_enable(0)
     assert f >= 0
     G.close()
+
+
+@pytest.mark.parametrize("scale", [11, 14])
+def test_topology_driven_mode(mf, scale):
+    """MF_MODE_TOPOLOGY (Sec. 5.2): same values, certified states."""
+    g = gen.rmat(scale=scale, seed=90 + scale)
+    G, _ = run_batches(mf, g, mixed(g, max(10, g.m // 200), 1, 500, scale, 3), mode=mf.MF_MODE_TOPOLOGY)
+    G.close()
