@@ -283,7 +283,7 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2511_05895_gb300 import MaxFlowGraph
+    from paper_2511_05895_gb300 import MaxFlowGraph, replicas
 
     g = gen.rmat(scale=SCALE, seed=SEED + 1000 * rank)
     cap = g.cap.copy()
@@ -337,11 +337,8 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     times = [a.elapsed_time(b) for a, b in events]          # ms
-    t_total = sum(times) / 1000.0
+    t_total = replicas.max_over_ranks(sum(times) / 1000.0, device="cuda")
     if dist:
-        tt = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
         dist.barrier()
     G.sync()
     flow_after = G.flow_value()
@@ -367,11 +364,7 @@ def main():
         G.apply_updates(ids, caps)
         G.flow_value()
         t_e2e += time.perf_counter() - t0
-    e2e_value = world * args.steps / t_e2e if world == 1 else None
-    if dist:
-        tt = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_value = world * args.steps / float(tt.item())
+    e2e_value = replicas.whole_job_rate(args.steps, t_e2e, device="cuda")
 
     # ---- dynamic vs static recompute per batch size ----------------------
     sizes = {}

@@ -335,3 +335,17 @@ def test_topology_driven_mode(mf, scale):
     g = gen.rmat(scale=scale, seed=90 + scale)
     G, _ = run_batches(mf, g, mixed(g, max(10, g.m // 200), 1, 500, scale, 3), mode=mf.MF_MODE_TOPOLOGY)
     G.close()
+
+
+@pytest.mark.slow
+def test_full_size_grid4096_rect_batches(mf):
+    """The 4096 x 4096 segmentation grid (16.8M vertices, s and t with one
+    arc per pixel) with rectangle batches of side 64-512: values equal to the
+    oracle and the certificate on the full state."""
+    g = gen.grid_segmentation(4096, 4096, seed=3)
+
+    def batches(cap):
+        for i in range(2):
+            yield gen.grid_rect_batch(g, seed=3, index=i)
+    G, _ = run_batches(mf, g, batches, kernel_cycles=4)
+    G.close()
