@@ -56,7 +56,8 @@ SEED = 1
 BYTES = {
     "bfs_arcs": 12,       # head 4 + mirrored residual 4 + height of the head 4
     "bfs_vertices": 20,   # row offsets 8 + height write 4 + queue write 4 + queue read 4
-    "height_init": 12,    # per vertex per BFS: excess 8 + height write 4
+    "height_init": 12,    # per vertex per BFS: excess 8 + height write 4 (+ 8 per vertex for
+                          # the deficit recount of a loop that ends without a final BFS)
     "pr_arcs": 12,        # residual 4 + head 4 + height of the head 4
     "pushes": 64,         # 4 int32 residual RMW (8 each) + 2 int64 excess RMW (16 each)
     "relabels": 4,
@@ -73,7 +74,8 @@ def algorithmic_bytes(st: dict, n: int) -> int:
     b = 0
     for k, w in BYTES.items():
         if k == "height_init":
-            b += w * n * (st["iterations"] + 1)
+            bfs_runs = st["iterations"] + (1 if st["exit_kind"] == 0 else 0)
+            b += w * n * bfs_runs + (8 * n if st["exit_kind"] == 1 else 0)
         else:
             b += w * st[k]
     return int(b)
@@ -318,7 +320,8 @@ def main():
     G.sync()
     stats_acc = {k: 0 for k in [b for b in BYTES if b != "height_init"] +
                  ["iterations", "bfs_levels", "t_batch_ns", "t_reset_ns", "t_bfs_ns", "t_pr_ns",
-                  "t_hub_ns", "t_ri_ns", "hub_cycles", "barriers", "bfs_bottom_up_levels", "pr_rounds"]}
+                  "t_hub_ns", "t_ri_ns", "hub_cycles", "barriers", "bfs_bottom_up_levels", "pr_rounds",
+                  "clean_exits"]}
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -333,7 +336,7 @@ def main():
         st = G.stats()
         per_step_bytes.append(algorithmic_bytes(st, g.n))
         for k in stats_acc:
-            stats_acc[k] += st[k]
+            stats_acc[k] += st[k] if k != "clean_exits" else int(st["exit_kind"] == 1)
     torch.cuda.synchronize()
     clk = clocks.stop()
     times = [a.elapsed_time(b) for a, b in events]          # ms

@@ -97,7 +97,7 @@ typedef struct mf_options {
 } mf_options;
 
 /* Counters of the last mf_solve / mf_apply_updates (device-side counts).
- *  iterations   BFS + push/relabel rounds of the device loop (Alg. 1/4 while)
+ *  iterations   loop iterations that ran PushRelabel (Alg. 1/4 while loop)
  *  bfs_levels   BFS levels over all iterations
  *  bfs_vertices vertices reached by the BFS (sum over iterations)
  *  bfs_arcs     arcs scanned by the BFS
@@ -117,7 +117,15 @@ typedef struct mf_options {
  *  pr_rounds    PushRelabel activation rounds (vertices made active by a push
  *               are processed in the next round of the same iteration)
  *  policy_*     last policy decision: kind 0 = repair, 1 = recompute; the
- *               KERNELCYCLES chosen; 1 if the learned policy fell back */
+ *               KERNELCYCLES chosen; 1 if the learned policy fell back
+ *  exit_kind    how the loop ended: 0 = a BFS found no active vertex; 1 = the
+ *               last PushRelabel/RemoveInvalidEdges round left no active
+ *               vertex under its own (valid) heights, so no final BFS ran;
+ *               2 = the batch only raised capacities of arcs that do not
+ *               cross the last exact cut, so the flow value cannot change
+ *               and no loop ran.  After 1 or 2 the heights are not the BFS
+ *               fixed point; mf_min_cut and mf_export_state recompute them
+ *               first (one BFS). */
 typedef struct mf_stats {
     int64_t flow;
     int64_t iterations;
@@ -149,7 +157,7 @@ typedef struct mf_stats {
     int32_t policy_kind;
     int32_t policy_kernel_cycles;
     int32_t policy_fallback;
-    int32_t reserved1;
+    int32_t exit_kind;
     int32_t status;
     int32_t kernel_cycles;
     int32_t grid_blocks;
@@ -241,8 +249,9 @@ int mf_sync(mf_graph *g);
 int mf_flow_value(mf_graph *g, int64_t *out);
 
 /* Minimum cut: side[v] = 1 if v is on the source side S = {h(v) >= n}
- * (Note 1 of Sec. 3), else 0.  side is [n] bytes, host or device per flags.
- * Synchronises. */
+ * (Note 1 of Sec. 3), else 0, with h the exact BFS heights (recomputed by one
+ * device BFS if the last solve stopped without one; see exit_kind).  side is
+ * [n] bytes, host or device per flags.  Synchronises. */
 int mf_min_cut(mf_graph *g, uint8_t *side, int32_t flags);
 
 /* Counters of the last solve/repair.  Synchronises. */
@@ -257,8 +266,9 @@ int mf_sizes(const mf_graph *g, int32_t *n, int64_t *m, int64_t *arcs);
 int mf_export_graph(mf_graph *g, int64_t *arc_row, int32_t *head, int32_t *rev, int32_t *cap);
 
 /* Checkpoint: copy residuals r [arcs] int32, excess [n] int64 and heights
- * [n] int32 out (host or device buffers per flags; any may be NULL).
- * Synchronises. */
+ * [n] int32 out (host or device buffers per flags; any may be NULL).  The
+ * heights are the exact BFS heights (recomputed first when needed, as for
+ * mf_min_cut).  Synchronises. */
 int mf_export_state(mf_graph *g, int32_t *r, int64_t *excess, int32_t *height, int32_t flags);
 
 /* Resume: load residuals, excess and heights previously exported from a
@@ -276,7 +286,7 @@ void mf_destroy(mf_graph *g);
  * another framework which owns all device memory through its own pool, or a
  * service path where allocations are forbidden after start-up -- and so
  * cannot use mf_create.  Instead of allocating, it works in one static
- * device array of 13,353,472 bytes (about 12.7 MiB) that every GPU which
+ * device array of 13,533,952 bytes (about 12.9 MiB) that every GPU which
  * loads this library holds until the process exits.
  *   n, arcs        vertices (2 .. 131072) and Bi-CSR arcs (0 .. 2097152);
  *                  larger graphs are rejected with MF_EINVAL
@@ -398,7 +408,12 @@ void mf_server_destroy(mf_server *s);
 /* Tracing: one record per grid barrier of the solve/repair kernel.
  *   phase  MF_PHASE_*; mode: BFS 0 top-down frontier, 1 top-down items of
  *          high-degree vertices, 2 bottom-up groups, 3 bottom-up items; hub
- *          cycles 0 set-up, 1 lowest-neighbour scan, 3 pushes
+ *          cycles 0 set-up, 1 lowest-neighbour scan, 3 pushes;
+ *          RemoveInvalidEdges: why the loop went on to another BFS, bits
+ *          1 the activation rounds reached their cap, 2 the hub cycles
+ *          reached theirs, 4 an arc was saturated, 8 a push re-activated a
+ *          high-degree vertex (0: it stopped; a height-init record of step 1,
+ *          the recount of the deficits, follows)
  *   iter   loop iteration (-1 before the loop), step: BFS level, activation
  *          round or hub cycle, count: frontier size, list size or items
  *   ns     device time since the previous barrier (globaltimer of CTA 0) */

@@ -39,7 +39,7 @@ class Stats(ctypes.Structure):
         "arcs", "t_batch_ns", "t_reset_ns", "t_bfs_ns", "t_pr_ns", "t_hub_ns", "t_ri_ns",
         "hub_cycles", "barriers", "bfs_bottom_up_levels", "pr_rounds")] + [
         (f, ctypes.c_int32) for f in ("policy_kind", "policy_kernel_cycles", "policy_fallback",
-                                      "reserved1")] + [(f, ctypes.c_int32) for f in ("status", "kernel_cycles", "grid_blocks",
+                                      "exit_kind")] + [(f, ctypes.c_int32) for f in ("status", "kernel_cycles", "grid_blocks",
                                                    "block_threads")]
 
     def as_dict(self):

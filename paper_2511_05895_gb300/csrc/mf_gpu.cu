@@ -51,12 +51,22 @@ constexpr int ST_WAIT = 4;     // a grid-barrier wait reached its time limit
 constexpr int ST_TIME = 8;     // the kernel ran past its wall-clock limit
 constexpr int ST_STICKY = ST_ITERS | ST_WAIT | ST_TIME;
 
-enum JobKind { JOB_SOLVE = 0, JOB_REPAIR = 1, JOB_RECOMPUTE = 2, JOB_AUTO = 3 };
+// JOB_REFRESH recomputes exact BFS heights (and the exact cut S = {h >= n})
+// for a state whose last solve stopped without a final BFS; it does nothing
+// when the heights are exact already.
+enum JobKind { JOB_SOLVE = 0, JOB_REPAIR = 1, JOB_RECOMPUTE = 2, JOB_AUTO = 3, JOB_REFRESH = 4 };
 
-// PushRelabel activation rounds per loop iteration, and the fewest
+// How the last solve/repair ended (mf_stats.exit_kind)
+enum ExitKind { EXIT_BFS = 0, EXIT_CLEAN = 1, EXIT_NO_CUT_CHANGE = 2 };
+
+// Fewest PushRelabel activation rounds per loop iteration, and the fewest
 // cooperative cycles the high-degree vertices get per iteration (see k_solve).
 constexpr int kMaxRounds = 16;
 constexpr int kMinHubCycles = 4;
+// PushRelabel passes per loop iteration (hub cycles, then activation rounds;
+// a pass that turns hubs active again hands them to the next pass)
+constexpr int kMaxPasses = 2;
+constexpr int kPassHubs = 32;   // most re-activated hubs a further pass takes
 
 constexpr int S_COUNT_MAX = 24;
 
@@ -67,8 +77,8 @@ struct Ctl {
     int status;           // ST_* bits                      } read together by
     int batch_err;        // (z) set by batch validation    } mf_flow_value
     long long flow;       // result of the last solve/repair }
-    unsigned bar_count;   // (z) grid barrier arrivals
-    unsigned bar_gen;     // grid barrier generation
+    unsigned bar_word;    // grid barrier: generation (high 16 bits), arrivals (z, low 16 bits)
+    unsigned bar_pad;
     int qcnt[3];          // (z) BFS frontier sizes, rotating by level
     int ccnt[3];          // (z) BFS chunk-item counts, rotating by level
     int gtk[3];           // (z) BFS frontier-group tickets, rotating by level
@@ -94,7 +104,16 @@ struct Ctl {
     float feat[12];       // features of the last batch the policy kernel saw
     int abort_loop;       // (z) set by thread 0 when the wall-clock limit passed
     int trace_n;          // trace records written by the current launch
+    int ri_moved[2];      // (z) RemoveInvalidEdges saturated an arc, by iteration parity
+    int phc[2];           // (z) hub lists of the next PushRelabel pass, by pass parity
+    int rhcnt;            // (z) RemoveInvalidEdges items of relabelled hubs
+    int pad2;
+    int inc_block;        // (z) the batch holds a decrement or an increment across the cut
+    int heights_exact;    // h is the BFS fixed point of the current residual graph
+    int cut_exact;        // {h >= n} is exactly the set that cannot reach a sink
+    int exit_kind;        // ExitKind of the last solve/repair
     long long st[S_COUNT_MAX];  // statistics, see enum Stat
+    long long st_aux[S_COUNT_MAX];  // where a JOB_REFRESH counts, keeping st intact
 };
 
 enum Stat {
@@ -125,6 +144,8 @@ struct DevGraph {
     int *qb0, *qb1, *wl;
     int2 *cb;
     int *hl, *hmode;          // active hubs; per-hub cycle state
+    int *hl2;                 // hub list of odd PushRelabel passes
+    int2 *hri;                // RemoveInvalidEdges items of relabelled hubs (vertex, first arc)
     int *hnit, *hdone;        // per-hub work items, and items finished in the cycle
     int2 *hcl;                // hub work items (hub index, first arc)
     int2 *hlv0, *hlv1;        // items of the hubs still active, per cycle (double buffer)
@@ -141,6 +162,9 @@ struct DevGraph {
 
 struct Job {
     int kind, k, flags, kc, mode;
+    int exact_exit;      // 1: stop only after a BFS finds no active vertex
+    long long *st;       // statistics array (Ctl::st, or Ctl::st_aux for JOB_REFRESH)
+    TraceRec *trace;     // trace records, or nullptr
     const int *k_dev;    // if set, the batch size is read from device memory
     long long max_iters;
     unsigned long long time_limit_ns;
@@ -152,6 +176,16 @@ struct Job {
 __device__ __forceinline__ int lcg(const int *p) { return __ldcg(p); }
 __device__ __forceinline__ long long lcg(const long long *p) { return __ldcg(p); }
 __device__ __forceinline__ int2 lcg(const int2 *p) { return __ldcg(p); }
+
+// Work items of a phase over the grid's warps: warp w starts with item w and
+// then takes tickets, offset by the warp count, so a phase with fewer items
+// than warps runs without any atomic and a large one stays balanced.  All 32
+// lanes call; returns the warp's next item.
+__device__ __forceinline__ int next_ticket(int *ticket, int nwarps) {
+    int t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(ticket, 1);
+    return __shfl_sync(0xffffffffu, t, 0) + nwarps;
+}
 
 __device__ __forceinline__ void add_ll(long long *p, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
@@ -214,19 +248,21 @@ __device__ __forceinline__ void warp_append(bool pred, int val, int *cnt, int *b
 // by one CTA.)  Every wait gives up after kWaitNs and sets ST_WAIT; returns
 // false when any CTA gave up (the kernel must then return).
 __device__ __forceinline__ bool grid_sync(Ctl *C) {
+    __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned gen = ld_acquire(&C->bar_gen);
+        // one word holds the generation and the arrivals: the arrival's
+        // atomic returns the generation to wait on, and the last CTA to
+        // arrive starts the next generation with zero arrivals
         __threadfence();
-        const unsigned arrived = atomicAdd(&C->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&C->bar_count, 0u);
+        const unsigned old = atomicAdd(&C->bar_word, 1u);
+        if ((old & 0xffffu) == gridDim.x - 1) {
             __threadfence();
-            atomicAdd(&C->bar_gen, 1u);
+            atomicAdd(&C->bar_word, 0x10000u - gridDim.x);
         } else {
             const unsigned long long t0 = gtimer();
             unsigned spins = 0;
-            while (ld_acquire(&C->bar_gen) == gen) {
+            while (((ld_acquire(&C->bar_word) ^ old) & 0xffff0000u) == 0) {
                 if ((++spins & 31u) == 0) {
                     if (__ldcg(&C->status) & ST_WAIT) break;
                     if (gtimer() - t0 > kWaitNs) {
@@ -238,9 +274,10 @@ __device__ __forceinline__ bool grid_sync(Ctl *C) {
             }
         }
         __threadfence();
+        ok = (__ldcg(&C->status) & ST_WAIT) == 0;
     }
     __syncthreads();
-    return (__ldcg(&C->status) & ST_WAIT) == 0;
+    return ok;
 }
 
 // ---------------------------------------------------------- BFS visiting --
@@ -509,6 +546,9 @@ struct ActList {
     int *list;
     unsigned stamp;
     unsigned rstamp;   // stamp of this loop iteration's relabel list
+    int *hcnt;         // the next pass's hub list (high-degree vertices a push
+    int *hlist;        //   turned active), its size and its stamp
+    unsigned hstamp;
 };
 
 // A vertex whose height PushRelabel raised joins the relabel list of the loop
@@ -520,16 +560,22 @@ __device__ __forceinline__ void note_relabel(const DevGraph &G, int u, unsigned 
 }
 
 // A push of d units raised e(v) from `old`: if v turned active (excess
-// positive, below height n, not s or t, degree <= kHubDeg) it joins the next
-// activation round.  All 32 lanes call.
+// positive, below height n, not s or t) it joins the next activation round
+// when its degree is <= kHubDeg, else the hub list of the next PushRelabel
+// pass.  All 32 lanes call.
 __device__ __forceinline__ void note_activation(const DevGraph &G, bool pushed, int v, long long old, long long d,
                                                 const ActList &AL) {
-    bool add = false;
+    bool add = false, add_hub = false;
     if (pushed && old <= 0 && old + d > 0 && v != G.s && v != G.t) {
-        if (lcg(&G.h[v]) < G.n && __ldg(&G.row[v + 1]) - __ldg(&G.row[v]) <= kHubDeg)
-            add = atomicExch(&G.astamp[v], AL.stamp) != AL.stamp;
+        if (lcg(&G.h[v]) < G.n) {
+            if (__ldg(&G.row[v + 1]) - __ldg(&G.row[v]) <= kHubDeg)
+                add = atomicExch(&G.astamp[v], AL.stamp) != AL.stamp;
+            else
+                add_hub = atomicExch(&G.astamp[v], AL.hstamp) != AL.hstamp;
+        }
     }
     warp_append(add, v, AL.cnt, AL.list);
+    warp_append(add_hub, v, AL.hcnt, AL.hlist);
 }
 
 // One round of a warp's arc scan: lane i holds arcs a0 + 32 j + i (j < kIlp)
@@ -736,7 +782,7 @@ __device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int 
 // every residual arc u -> v with h(u) > h(v) + 1 is saturated, moving its
 // residual as excess to v.  Returns this lane's share of the excess moved.
 __device__ __forceinline__ long long remove_invalid_range(const DevGraph &G, int hu, int a0, int a1,
-                                                          Counters &K) {
+                                                          int *moved_flag, Counters &K) {
     const int lane = threadIdx.x & 31;
     long long moved = 0;
     for (int b0 = a0; b0 < a1; b0 += 32 * kIlp) {
@@ -749,17 +795,18 @@ __device__ __forceinline__ long long remove_invalid_range(const DevGraph &G, int
                 push_arc(G, b0 + 32 * j + lane, R.v[j], R.ra[j]);
                 moved += R.ra[j];
                 ++K.ri_moves;
+                *moved_flag = 1;
             }
         }
     }
     return moved;
 }
 
-__device__ __forceinline__ void remove_invalid_warp(const DevGraph &G, int u, Counters &K) {
+__device__ __forceinline__ void remove_invalid_warp(const DevGraph &G, int u, int *moved_flag, Counters &K) {
     const int lane = threadIdx.x & 31;
     const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
     const int hu = __shfl_sync(kFull, lane == 0 ? lcg(&G.h[u]) : 0, 0);
-    const long long moved = warp_sum(remove_invalid_range(G, hu, beg, end, K));
+    const long long moved = warp_sum(remove_invalid_range(G, hu, beg, end, moved_flag, K));
     if (lane == 0 && moved) add_ll(&G.e[u], -moved);
 }
 
@@ -767,18 +814,20 @@ __device__ __forceinline__ void remove_invalid_warp(const DevGraph &G, int u, Co
 // Grid barrier inside k_solve; CTA 0's thread 0 charges the time since the
 // previous barrier to a phase bucket of the statistics and, when tracing is
 // on, appends a record (phase, loop iteration, step, mode, count, time).
+#define ST (J.st)
+#define TR (J.trace)
 #define MF_SYNC_T(bucket, step, mode, aux)                                    \
     do {                                                                      \
         if (!grid_sync(C)) return;                                            \
         if (gtid == 0) {                                                      \
             const unsigned long long now_ = gtimer();                         \
             const long long dt_ = (long long)(now_ - tprev);                  \
-            C->st[bucket] += dt_;                                             \
-            C->st[S_BARRIERS] += 1;                                           \
-            if (G.trace) {                                                    \
+            ST[bucket] += dt_;                                                \
+            ST[S_BARRIERS] += 1;                                              \
+            if (TR) {                                                         \
                 const int k_ = C->trace_n++;                                  \
                 if (k_ < G.trace_cap)                                         \
-                    G.trace[k_] = TraceRec{(short)(bucket), (short)(mode),    \
+                    TR[k_] = TraceRec{(short)(bucket), (short)(mode),    \
                                            (int)it, (int)(step), (int)(aux), dt_}; \
             }                                                                 \
             tprev = now_;                                                     \
@@ -809,17 +858,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         kind = lcg(&C->pol_kind);
         kc = lcg(&C->pol_kc);
     }
+    if (kind == JOB_REFRESH && lcg(&C->heights_exact)) return;
+    const bool batch_job = kind == JOB_REPAIR || kind == JOB_RECOMPUTE;
     const int kb = J.k_dev ? lcg(J.k_dev) : J.k;          // batch entries
     const unsigned seq = __ldcg(&C->bseq) + 1u;           // this batch's stamp
     if (gtid == 0) {
-        for (int i = 0; i < S_COUNT; ++i) C->st[i] = 0;
-        C->st[S_BATCH] = kind == JOB_SOLVE ? 0 : kb;
+        for (int i = 0; i < S_COUNT; ++i) ST[i] = 0;
+        ST[S_BATCH] = batch_job ? kb : 0;
         C->t_start = gtimer();
-        C->trace_n = 0;
+        if (TR) C->trace_n = 0;
     }
 
     // ---- batch: validate, then apply (Algorithm 5) ----------------------
-    if (kind != JOB_SOLVE) {
+    bool fast = false;   // pure-increment batch that cannot change the cut
+    if (batch_job) {
         for (long long i = gtid; i < kb; i += gthreads) {
             const int eid = J.ids[i];
             bool bad = eid < 0 || eid >= G.m;
@@ -858,13 +910,24 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             if (a >= 0 && d != 0) {
                 atomicAdd(&G.cap[a], d);
                 if (kind == JOB_REPAIR) {
+                    const int b = __ldg(&G.rev[a]);
                     atomicAdd(&G.r[a], d);
-                    atomicAdd(&G.rr[__ldg(&G.rev[a])], d);
+                    atomicAdd(&G.rr[b], d);
+                    // an increment can raise the flow only on an arc from
+                    // the side that cannot reach a sink to the side that can
+                    if (d < 0 || (lcg(&G.h[__ldg(&G.head[b])]) >= n && lcg(&G.h[__ldg(&G.head[a])]) < n))
+                        C->inc_block = 1;
                 }
             }
         }
         MF_SYNC(S_T_BATCH);
-        if (kind == JOB_REPAIR) {
+        // With the exact cut S = {h >= n} of the previous state (no residual
+        // arc from S to T), increments on arcs that do not go from S to T
+        // leave that cut saturated and its capacity unchanged, so the flow
+        // value stays the same and the state stays terminal (Sec. 4: only
+        // changes on the cut's arcs can change the maximum).
+        fast = kind == JOB_REPAIR && lcg(&C->cut_exact) && !lcg(&C->inc_block);
+        if (kind == JOB_REPAIR && !fast) {
             // flow above the new capacity goes back: the tail keeps it as
             // excess, the head becomes deficient (Alg. 5, lines 4-11; the
             // excess update is the exact incremental form of Alg. 4 line 2).
@@ -889,7 +952,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     }
 
     // ---- zero flow (Algorithm 1, first two loops) ------------------------
-    if (kind != JOB_REPAIR) {
+    if (kind == JOB_SOLVE || kind == JOB_RECOMPUTE) {
         for (long long a = gtid; a < G.A; a += gthreads) {
             G.r[a] = lcg(&G.cap[a]);
             G.rr[a] = lcg(&G.cap[__ldg(&G.rev[a])]);
@@ -899,7 +962,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     }
 
     // ---- saturate the source arcs (Alg. 1 third loop, Alg. 4 lines 3-7) --
-    {
+    // (on the fast path every source arc that regains residual leads into
+    // S, so the moved excess stays on vertices that cannot reach a sink)
+    if (kind != JOB_REFRESH) {
         long long moved = 0;
         const int a0 = __ldg(&G.row[s]), a1 = __ldg(&G.row[s + 1]);
         for (long long a = a0 + gtid; a < a1; a += gthreads) {
@@ -921,8 +986,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     }
 
     // ---- device loop (Algorithm 4 while-loop) ----------------------------
-    it = 0;
-    for (;; ++it) {
+    bool early = false;   // stopped when PushRelabel left no active vertex
+    unsigned snext = stamp_base;   // next unused activation stamp
+    for (it = 0; !fast; ++it) {
         const int par = (int)(it & 1);
         // height init: t and deficient vertices are sinks (height 0), all
         // others n; the sinks form BFS level 0.
@@ -935,6 +1001,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             C->acnt[0] = C->acnt[1] = C->acnt[2] = 0;
             C->rtk[0] = C->rtk[1] = C->rtk[2] = 0;
             C->rlcnt = 0;
+            C->rhcnt = 0;
+            C->phc[1] = 0;
             C->wcnt = 0;
             C->hcnt = 0;
             C->hccnt = 0;
@@ -963,6 +1031,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             if (lane == 0 && rdeg) add_ll(&C->asum[0], rdeg);
         }
         MF_SYNC_T(S_T_RESET, 0, 0, lcg(&C->qcnt[0]));
+        // the flags of the next iteration: their last readers (the previous
+        // iteration's exit test) are all past this barrier
+        if (gtid == 0) C->ri_moved[par ^ 1] = 0;
 
         // backward BFS from the sinks over residual arcs (global relabel),
         // level-synchronous and direction-optimising: top-down from the
@@ -989,26 +1060,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 C->gtk[(L + 1) % 3] = 0;
                 C->ctk[(L + 1) % 3] = 0;
                 C->asum[(L + 2) % 3] = 0;
-                if (bottom_up) C->st[S_BU_LEVELS] += 1;
+                if (bottom_up) ST[S_BU_LEVELS] += 1;
             }
             if (bottom_up) {
-                // groups of 32 consecutive vertex ids, handed out by an atomic ticket
+                // groups of 32 consecutive vertex ids (warp w first, then tickets)
                 const int groups = (n + 31) / 32;
-                for (;;) {
-                    int grp = 0;
-                    if (lane == 0) grp = atomicAdd(&C->gtk[L % 3], 1);
-                    grp = __shfl_sync(kFull, grp, 0);
-                    if (grp >= groups) break;
+                for (int grp = gwarp; grp < groups; grp = next_ticket(&C->gtk[L % 3], nwarps))
                     bfs_bottom_up_group(G, grp * 32, L, ncnt, NF, asum, ccnt, K);
-                }
             } else {
-                // groups of 32 frontier vertices, handed out by an atomic ticket
-                for (;;) {
-                    int grp = 0;
-                    if (lane == 0) grp = atomicAdd(&C->gtk[L % 3], 1);
-                    const int base = __shfl_sync(kFull, grp, 0) * 32;
-                    if (base >= cur) break;
-                    const int idx = base + lane;
+                // groups of 32 frontier vertices (warp w first, then tickets)
+                for (int grp = gwarp; grp * 32 < cur; grp = next_ticket(&C->gtk[L % 3], nwarps)) {
+                    const int idx = grp * 32 + lane;
                     int beg = 0, deg = 0;
                     if (idx < cur) {
                         const int u = lcg(&F[idx]);
@@ -1027,11 +1089,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             MF_SYNC_T(S_T_BFS, L, bottom_up ? 2 : 0, cur);
             const int nch = lcg(ccnt);
             if (nch > 0) {
-                for (;;) {
-                    int c = 0;
-                    if (lane == 0) c = atomicAdd(&C->ctk[L % 3], 1);
-                    c = __shfl_sync(kFull, c, 0);
-                    if (c >= nch) break;
+                for (int c = gwarp; c < nch; c = next_ticket(&C->ctk[L % 3], nwarps)) {
                     const int2 item = lcg(&G.cb[c]);
                     if (bottom_up) {
                         bfs_bottom_up_item(G, item, L, ncnt, NF, asum, K);
@@ -1053,7 +1111,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             }
             ++L;
         }
-        if (gtid == 0) C->st[S_LEVELS] += L;
+        if (gtid == 0) ST[S_LEVELS] += L;
 
         // termination: no active vertex under the fresh BFS heights
         const int nw = lcg(&C->wcnt);
@@ -1067,233 +1125,329 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             if (gtid == 0) atomicOr(&C->status, ST_TIME);
             break;
         }
-        if (gtid == 0) C->st[S_WL] += nh;
 
-        // PushRelabel (Alg. 2).  High-degree vertices first, together in
-        // kPrChunk-arc items over the whole grid; then the worklist, one warp
-        // per vertex, in activation rounds: a vertex that a push turns active
-        // joins the list of the next round instead of waiting for the next
-        // BFS.  Rounds are separated by grid barriers, so no vertex is ever
-        // processed by two warps at once.
-        const unsigned sbase = stamp_base + (unsigned)it * (kMaxRounds + 1);
+        // PushRelabel (Alg. 2), in passes.  A pass serves the high-degree
+        // vertices of its hub list together, in kPrChunk-arc items over the
+        // whole grid (cooperative cycles), and then the worklist, one warp per
+        // vertex, in activation rounds: a vertex that a push turns active joins
+        // the list of the next round instead of waiting for the next BFS.
+        // Cycles and rounds are separated by grid barriers, so no vertex is
+        // ever processed by two warps at once.  High-degree vertices that a
+        // pass turns active again form the hub list of the next pass.
+        const unsigned rstamp_it = snext++;   // relabel-list stamp of this iteration
         if (gtid == 0) {
             C->qcnt[0] = 0;
             C->asum[0] = 0;
         }
-        const ActList AL0{&C->wcnt, G.wl, sbase, sbase};
-        int nhc = 0;
-        if (nh > 0) {
-            for (int i = gwarp; i < nh; i += nwarps) {
-                const int u = lcg(&G.hl[i]);
-                const int beg = __ldg(&G.row[u]);
-                const int nc = (__ldg(&G.row[u + 1]) - beg + kPrChunk - 1) / kPrChunk;
-                int pos = 0;
-                if (lane == 0) {
-                    pos = atomicAdd(&C->hccnt, nc);
-                    G.hkey[i] = ~0ull;
-                    G.hmode[i] = 0;
-                    G.hnit[i] = nc;
-                    G.hdone[i] = 0;
+        bool rounds_clean = true;   // the last activation round left no active vertex
+        bool hubs_clean = true;     // the last hub cycle left no hub active
+        int pend = 0;               // hubs that the last pass turned active
+        // Rounds per pass: kMaxRounds, and past that, while the list holds at
+        // most one vertex per warp, as many as the BFS just run had levels --
+        // such a round costs about what a BFS level costs, so on deep graphs
+        // (grids) finishing a few active vertices by rounds is cheaper than
+        // another global relabel.
+        const int max_rounds = L > kMaxRounds ? L : kMaxRounds;
+        for (int pass = 0; pass < kMaxPasses; ++pass) {
+            const int *HL = (pass & 1) ? G.hl2 : G.hl;
+            const int nhp = pass == 0 ? nh : pend;
+            const unsigned wstamp = snext++;   // this pass's round-0 list
+            const unsigned hstamp = snext++;   // the next pass's hub list
+            int *const pcnt = &C->phc[(pass + 1) & 1];
+            // pass 0 appends to phc[1] and starts its rounds on the counters
+            // zeroed at the iteration's start; a later pass always has hubs,
+            // so its set-up barrier comes before any use of what is zeroed
+            // here (the previous pass's rounds ended with an empty list)
+            if (gtid == 0) {
+                if (pass > 0) {
+                    *pcnt = 0;
+                    C->wcnt = 0;
+                    C->acnt[0] = C->acnt[1] = C->acnt[2] = 0;
+                    C->rtk[0] = C->rtk[1] = C->rtk[2] = 0;
                 }
-                pos = __shfl_sync(kFull, pos, 0);
-                for (int c = lane; c < nc; c += 32) G.hcl[pos + c] = make_int2(i, beg + c * kPrChunk);
+                C->hub_act[0] = C->hub_act[1] = 0;
+                C->hlc[0] = C->hlc[1] = 0;
+                ST[S_WL] += nhp;
             }
-            MF_SYNC_T(S_T_HUB, -1, 0, nh);
-            nhc = lcg(&C->hccnt);
-            const int hub_cycles = kc > kMinHubCycles ? kc : kMinHubCycles;
-            for (int c = 0; c < hub_cycles; ++c) {
-                if (gtid == 0) C->st[S_HUB_CYCLES] += 1;
-                // H1: lowest residual neighbour of every unfinished hub; the
-                // warp that completes a hub's last item takes the hub's
-                // decision (push at the lowest height, relabel, or finish)
-                // the cycle's items: all hub items in cycle 0, afterwards the
-                // items of the hubs still active after the previous cycle
-                const int2 *items = c == 0 ? G.hcl : ((c - 1) & 1 ? G.hlv1 : G.hlv0);
-                const int nitems = c == 0 ? nhc : lcg(&C->hlc[(c - 1) & 1]);
-                for (int w = gwarp; w < nitems; w += nwarps) {
-                    const int2 item = lcg(&items[w]);
-                    const int i = item.x;
-                    if (lcg(&G.hmode[i]) < 0) continue;
-                    const int u = lcg(&G.hl[i]);
+            const ActList AL0{&C->wcnt, G.wl, wstamp, rstamp_it, pcnt, (pass & 1) ? G.hl : G.hl2, hstamp};
+            bool pass_hubs_clean = true;
+            if (nhp > 0) {
+                pass_hubs_clean = false;
+                for (int i = gwarp; i < nhp; i += nwarps) {
+                    const int u = lcg(&HL[i]);
                     const int beg = __ldg(&G.row[u]);
-                    const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
-                    unsigned long long best = ~0ull;
-                    for (int a0 = item.y; a0 < a1; a0 += 32 * kIlp) {
-                        ArcRound R;
-                        load_round(G, a0, a1, R);
-                        K.pr_arcs += round_arcs(a0, a1);
-                        const unsigned long long k = round_min_key(R, a0, beg);
-                        best = k < best ? k : best;
-                    }
-                    best = warp_min(best);
-                    int decided = -2;   // -2: not the deciding warp; else the hub's mode
+                    const int nc = (__ldg(&G.row[u + 1]) - beg + kPrChunk - 1) / kPrChunk;
+                    int pos = 0;
                     if (lane == 0) {
-                        G.hikey[w] = (unsigned)(best >> 32);   // lowest height in this item
-                        if (best != ~0ull) atomicMin(&G.hkey[i], best);
-                        __threadfence();
-                        if (atomicAdd(&G.hdone[i], 1) == lcg(&G.hnit[i]) - 1) {
+                        pos = atomicAdd(&C->hccnt, nc);
+                        G.hkey[i] = ~0ull;
+                        G.hmode[i] = 0;
+                        G.hnit[i] = nc;
+                        G.hdone[i] = 0;
+                    }
+                    pos = __shfl_sync(kFull, pos, 0);
+                    for (int c = lane; c < nc; c += 32) G.hcl[pos + c] = make_int2(i, beg + c * kPrChunk);
+                }
+                MF_SYNC_T(S_T_HUB, -1, 0, nhp);
+                const int nhc = lcg(&C->hccnt);
+                const int hub_cycles = kc > kMinHubCycles ? kc : kMinHubCycles;
+                for (int c = 0; c < hub_cycles; ++c) {
+                    if (gtid == 0) ST[S_HUB_CYCLES] += 1;
+                    // H1: lowest residual neighbour of every unfinished hub; the
+                    // warp that completes a hub's last item takes the hub's
+                    // decision (push at the lowest height, relabel, or finish)
+                    // the cycle's items: all hub items in cycle 0, afterwards the
+                    // items of the hubs still active after the previous cycle
+                    const int2 *items = c == 0 ? G.hcl : ((c - 1) & 1 ? G.hlv1 : G.hlv0);
+                    const int nitems = c == 0 ? nhc : lcg(&C->hlc[(c - 1) & 1]);
+                    for (int w = gwarp; w < nitems; w += nwarps) {
+                        const int2 item = lcg(&items[w]);
+                        const int i = item.x;
+                        if (lcg(&G.hmode[i]) < 0) continue;
+                        const int u = lcg(&HL[i]);
+                        const int beg = __ldg(&G.row[u]);
+                        const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
+                        // no push or relabel runs during H1, so every item of a hub
+                        // sees the same e(u), h(u): the items of a hub that is no
+                        // longer active skip the scan and only arrive
+                        const bool live = lcg(&G.e[u]) > 0 && lcg(&G.h[u]) < n;
+                        unsigned long long best = ~0ull;
+                        for (int a0 = item.y; live && a0 < a1; a0 += 32 * kIlp) {
+                            ArcRound R;
+                            load_round(G, a0, a1, R);
+                            K.pr_arcs += round_arcs(a0, a1);
+                            const unsigned long long k = round_min_key(R, a0, beg);
+                            best = k < best ? k : best;
+                        }
+                        best = warp_min(best);
+                        int decided = -2;   // -2: not the deciding warp; else the hub's mode
+                        bool relabelled = false;
+                        if (lane == 0) {
+                            G.hikey[w] = (unsigned)(best >> 32);   // lowest height in this item
+                            if (best != ~0ull) atomicMin(&G.hkey[i], best);
                             __threadfence();
-                            const int hu = lcg(&G.h[u]);
-                            const long long eu = lcg(&G.e[u]);
-                            const unsigned long long key = __ldcg(&G.hkey[i]);
-                            G.hkey[i] = ~0ull;
-                            G.hdone[i] = 0;
-                            int mode;
-                            if (hu >= n || eu <= 0) {
-                                mode = -1;
-                            } else if (key == ~0ull) {
-                                G.h[u] = n;
-                                ++K.relabel;
-                                mode = -1;
-                            } else {
-                                const int hh = (int)(key >> 32);
-                                if (hu > hh) {
-                                    mode = hh + 1;          // push to the arcs at height hh
-                                    G.hrem[i] = eu;
-                                } else {
-                                    G.h[u] = hh + 1;
+                            if (atomicAdd(&G.hdone[i], 1) == lcg(&G.hnit[i]) - 1) {
+                                __threadfence();
+                                const int hu = lcg(&G.h[u]);
+                                const long long eu = lcg(&G.e[u]);
+                                const unsigned long long key = __ldcg(&G.hkey[i]);
+                                G.hkey[i] = ~0ull;
+                                G.hdone[i] = 0;
+                                int mode;
+                                if (hu >= n || eu <= 0) {
+                                    mode = -1;
+                                } else if (key == ~0ull) {
+                                    G.h[u] = n;
                                     ++K.relabel;
-                                    mode = 0;
+                                    relabelled = true;
+                                    mode = -1;
+                                } else {
+                                    const int hh = (int)(key >> 32);
+                                    if (hu > hh) {
+                                        mode = hh + 1;          // push to the arcs at height hh
+                                        G.hrem[i] = eu;
+                                    } else {
+                                        G.h[u] = hh + 1;
+                                        ++K.relabel;
+                                        relabelled = true;
+                                        mode = 0;
+                                    }
                                 }
+                                G.hmode[i] = mode;
+                                if (mode >= 0) atomicAdd(&C->hub_act[c & 1], 1);
+                                decided = mode;
+                                // a relabelled hub's items join the iteration's
+                                // RemoveInvalidEdges list once
+                                if (relabelled && atomicExch(&G.rstamp[u], rstamp_it) == rstamp_it)
+                                    relabelled = false;
                             }
-                            G.hmode[i] = mode;
-                            if (mode >= 0) atomicAdd(&C->hub_act[c & 1], 1);
-                            decided = mode;
+                        }
+                        // a hub that stays active takes all its items into the
+                        // next cycle's list, written by the warp that decided it
+                        decided = __shfl_sync(kFull, decided, 0);
+                        relabelled = __shfl_sync(kFull, relabelled, 0);
+                        if (decided >= 0 || relabelled) {
+                            const int nit = lcg(&G.hnit[i]);
+                            int pos = 0, rpos = 0;
+                            if (lane == 0) {
+                                if (decided >= 0) pos = atomicAdd(&C->hlc[c & 1], nit);
+                                if (relabelled) rpos = atomicAdd(&C->rhcnt, nit);
+                            }
+                            pos = __shfl_sync(kFull, pos, 0);
+                            rpos = __shfl_sync(kFull, rpos, 0);
+                            int2 *next_items = c & 1 ? G.hlv1 : G.hlv0;
+                            for (int q = lane; q < nit; q += 32) {
+                                if (decided >= 0) next_items[pos + q] = make_int2(i, beg + q * kPrChunk);
+                                if (relabelled) G.hri[rpos + q] = make_int2(u, beg + q * kPrChunk);
+                            }
                         }
                     }
-                    // a hub that stays active takes all its items into the
-                    // next cycle's list, written by the warp that decided it
-                    decided = __shfl_sync(kFull, decided, 0);
-                    if (decided >= 0) {
-                        const int nit = lcg(&G.hnit[i]);
-                        int pos = 0;
-                        if (lane == 0) pos = atomicAdd(&C->hlc[c & 1], nit);
-                        pos = __shfl_sync(kFull, pos, 0);
-                        int2 *next_items = c & 1 ? G.hlv1 : G.hlv0;
-                        for (int q = lane; q < nit; q += 32) next_items[pos + q] = make_int2(i, beg + q * kPrChunk);
+                    MF_SYNC_T(S_T_HUB, c, 1, nitems);
+                    // hub_act[(c+1)&1] was last read by the exit test of cycle c-1,
+                    // which every thread has passed once it is past the H1 barrier;
+                    // likewise the item count of the set-up, read before H1
+                    if (gtid == 0) {
+                        C->hub_act[(c + 1) & 1] = 0;
+                        if (c == 0) C->hccnt = 0;
+                    }
+                    // H3: pushes along the lowest arcs; each warp reserves its share
+                    // of the hub's excess with one atomic
+                    // hlc[(c+1)&1] counted the list of cycle c-1, read before H1
+                    if (gtid == 0) C->hlc[(c + 1) & 1] = 0;
+                    for (int w = gwarp; w < nitems; w += nwarps) {
+                        const int2 item = lcg(&items[w]);
+                        const int mode = lcg(&G.hmode[item.x]);
+                        if (mode <= 0) continue;
+                        if (lcg(reinterpret_cast<const int *>(&G.hikey[w])) != mode - 1) continue;  // no arc at h^ here
+                        const int hh = mode - 1;
+                        const int u = lcg(&HL[item.x]);
+                        const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
+                        long long sent = 0;
+                        for (int a0 = item.y; a0 < a1; a0 += 32 * kIlp) {
+                            ArcRound R;
+                            load_round(G, a0, a1, R);
+                            K.pr_arcs += round_arcs(a0, a1);
+                            int ra[kIlp];
+                            long long incl[kIlp], tot = 0;
+#pragma unroll
+                            for (int j = 0; j < kIlp; ++j) {
+                                ra[j] = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
+                                incl[j] = warp_incl_scan(ra[j]) + tot;   // arc order: round j, then lane
+                                tot = __shfl_sync(kFull, incl[j], 31);
+                            }
+                            if (tot == 0) continue;
+                            long long old = 0;
+                            if (lane == 0)
+                                old = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&G.hrem[item.x]),
+                                                           (unsigned long long)(-tot));
+                            old = __shfl_sync(kFull, old, 0);
+                            if (old <= 0) break;
+#pragma unroll
+                            for (int j = 0; j < kIlp; ++j) {
+                                long long d = old - (incl[j] - ra[j]);
+                                d = d < 0 ? 0 : (d > ra[j] ? ra[j] : d);
+                                long long prev = 0;
+                                if (d > 0) {
+                                    prev = push_arc(G, a0 + 32 * j + lane, R.v[j], (int)d);
+                                    sent += d;
+                                    ++K.push;
+                                }
+                                note_activation(G, d > 0, R.v[j], prev, d, AL0);
+                            }
+                        }
+                        sent = warp_sum(sent);
+                        if (lane == 0 && sent) add_ll(&G.e[u], -sent);
+                    }
+                    MF_SYNC_T(S_T_HUB, c, 3, lcg(&C->hub_act[c & 1]));
+                    if (lcg(&C->hub_act[c & 1]) == 0) {
+                        pass_hubs_clean = true;
+                        break;
                     }
                 }
-                MF_SYNC_T(S_T_HUB, c, 1, nitems);
-                // hub_act[(c+1)&1] was last read by the exit test of cycle c-1,
-                // which every thread has passed once it is past the H1 barrier
-                if (gtid == 0) C->hub_act[(c + 1) & 1] = 0;
-                // H3: pushes along the lowest arcs; each warp reserves its share
-                // of the hub's excess with one atomic
-                // hlc[(c+1)&1] counted the list of cycle c-1, read before H1
-                if (gtid == 0) C->hlc[(c + 1) & 1] = 0;
-                for (int w = gwarp; w < nitems; w += nwarps) {
-                    const int2 item = lcg(&items[w]);
-                    const int mode = lcg(&G.hmode[item.x]);
-                    if (mode <= 0) continue;
-                    if (lcg(reinterpret_cast<const int *>(&G.hikey[w])) != mode - 1) continue;  // no arc at h^ here
-                    const int hh = mode - 1;
-                    const int u = lcg(&G.hl[item.x]);
-                    const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
-                    long long sent = 0;
-                    for (int a0 = item.y; a0 < a1; a0 += 32 * kIlp) {
-                        ArcRound R;
-                        load_round(G, a0, a1, R);
-                        K.pr_arcs += round_arcs(a0, a1);
-                        int ra[kIlp];
-                        long long incl[kIlp], tot = 0;
-#pragma unroll
-                        for (int j = 0; j < kIlp; ++j) {
-                            ra[j] = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
-                            incl[j] = warp_incl_scan(ra[j]) + tot;   // arc order: round j, then lane
-                            tot = __shfl_sync(kFull, incl[j], 31);
-                        }
-                        if (tot == 0) continue;
-                        long long old = 0;
-                        if (lane == 0)
-                            old = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&G.hrem[item.x]),
-                                                       (unsigned long long)(-tot));
-                        old = __shfl_sync(kFull, old, 0);
-                        if (old <= 0) break;
-#pragma unroll
-                        for (int j = 0; j < kIlp; ++j) {
-                            long long d = old - (incl[j] - ra[j]);
-                            d = d < 0 ? 0 : (d > ra[j] ? ra[j] : d);
-                            long long prev = 0;
-                            if (d > 0) {
-                                prev = push_arc(G, a0 + 32 * j + lane, R.v[j], (int)d);
-                                sent += d;
-                                ++K.push;
-                            }
-                            note_activation(G, d > 0, R.v[j], prev, d, AL0);
-                        }
-                    }
-                    sent = warp_sum(sent);
-                    if (lane == 0 && sent) add_ll(&G.e[u], -sent);
-                }
-                MF_SYNC_T(S_T_HUB, c, 3, lcg(&C->hub_act[c & 1]));
-                if (lcg(&C->hub_act[c & 1]) == 0) break;
             }
-        }
-        {
+            bool pass_rounds_clean = true;
             int cnt = lcg(&C->wcnt);
-            const int *list = G.wl;
-            for (int rd = 0;; ++rd) {
-                int *nlist = (rd & 1) ? G.qb0 : G.qb1;
-                const ActList AL{&C->acnt[(rd + 1) % 3], nlist, sbase + (unsigned)rd + 1, sbase};
-                if (gtid == 0) {
-                    C->acnt[(rd + 2) % 3] = 0;
-                    C->rtk[(rd + 1) % 3] = 0;
-                    C->st[S_ROUNDS] += 1;
-                    C->st[S_WL] += cnt;
-                }
-                if (rd == 0 && J.mode == MF_MODE_TOPOLOGY) {
-                    // topology-driven (Sec. 5.2): every vertex id is visited;
-                    // each warp takes 32 ids and serves the active ones
-                    for (;;) {
-                        int grp = 0;
-                        if (lane == 0) grp = atomicAdd(&C->rtk[0], 1);
-                        const int base = __shfl_sync(kFull, grp, 0) * 32;
-                        if (base >= n) break;
-                        const int v = base + lane;
-                        bool act = false;
-                        if (v < n && v != s && v != t && __ldg(&G.row[v + 1]) - __ldg(&G.row[v]) <= kHubDeg)
-                            act = lcg(&G.h[v]) < n && lcg(&G.e[v]) > 0;
-                        unsigned mask = __ballot_sync(kFull, act);
-                        while (mask) {
-                            const int j = __ffs(mask) - 1;
-                            mask &= mask - 1u;
-                            push_relabel_warp(G, base + j, kc, AL, K);
+            if (cnt > 0 || (pass == 0 && J.mode == MF_MODE_TOPOLOGY)) {
+                pass_rounds_clean = false;
+                const int *list = G.wl;
+                for (int rd = 0;; ++rd) {
+                    int *nlist = (rd & 1) ? G.qb0 : G.qb1;
+                    const ActList AL{&C->acnt[(rd + 1) % 3], nlist, snext++, rstamp_it, pcnt, AL0.hlist, hstamp};
+                    if (gtid == 0) {
+                        C->acnt[(rd + 2) % 3] = 0;
+                        C->rtk[(rd + 1) % 3] = 0;
+                        ST[S_ROUNDS] += 1;
+                        ST[S_WL] += cnt;
+                    }
+                    if (rd == 0 && pass == 0 && J.mode == MF_MODE_TOPOLOGY) {
+                        // topology-driven (Sec. 5.2): every vertex id is visited;
+                        // each warp takes 32 ids and serves the active ones
+                        for (int grp = gwarp; grp * 32 < n; grp = next_ticket(&C->rtk[0], nwarps)) {
+                            const int base = grp * 32;
+                            const int v = base + lane;
+                            bool act = false;
+                            if (v < n && v != s && v != t && __ldg(&G.row[v + 1]) - __ldg(&G.row[v]) <= kHubDeg)
+                                act = lcg(&G.h[v]) < n && lcg(&G.e[v]) > 0;
+                            unsigned mask = __ballot_sync(kFull, act);
+                            while (mask) {
+                                const int j = __ffs(mask) - 1;
+                                mask &= mask - 1u;
+                                push_relabel_warp(G, base + j, kc, AL, K);
+                            }
                         }
+                    } else {
+                        for (int i = gwarp; i < cnt; i = next_ticket(&C->rtk[rd % 3], nwarps))
+                            push_relabel_warp(G, lcg(&list[i]), kc, AL, K);
                     }
-                } else {
-                    for (;;) {
-                        int i = 0;
-                        if (lane == 0) i = atomicAdd(&C->rtk[rd % 3], 1);
-                        i = __shfl_sync(kFull, i, 0);
-                        if (i >= cnt) break;
-                        push_relabel_warp(G, lcg(&list[i]), kc, AL, K);
-                    }
+                    MF_SYNC_T(S_T_PRW, rd, 0, cnt);
+                    cnt = lcg(AL.cnt);
+                    list = nlist;
+                    if (cnt == 0) pass_rounds_clean = true;
+                    if (cnt == 0 || rd + 1 >= max_rounds || (rd + 1 >= kMaxRounds && cnt > nwarps)) break;
                 }
-                MF_SYNC_T(S_T_PRW, rd, 0, cnt);
-                cnt = lcg(AL.cnt);
-                list = nlist;
-                if (cnt == 0 || rd + 1 >= kMaxRounds) break;
             }
+            hubs_clean = pass_hubs_clean;
+            rounds_clean = pass_rounds_clean;
+            pend = lcg(pcnt);   // every append to it came before the pass's last barrier
+            // another pass only for a few re-activated hubs: a large set of
+            // them is better served after a global relabel
+            if (pend == 0 || pend > kPassHubs || !pass_hubs_clean || !pass_rounds_clean) break;
         }
 
-        // RemoveInvalidEdges (Alg. 3): relabelled vertices by warps, hubs by items
+        // RemoveInvalidEdges (Alg. 3): relabelled vertices by warps,
+        // relabelled hubs by items
         const int nrl = lcg(&C->rlcnt);
-        for (int i = gwarp; i < nrl; i += nwarps) remove_invalid_warp(G, lcg(&G.rl[i]), K);
-        for (int w = gwarp; w < nhc; w += nwarps) {
-            const int2 item = lcg(&G.hcl[w]);
-            const int u = lcg(&G.hl[item.x]);
+        for (int i = gwarp; i < nrl; i += nwarps) remove_invalid_warp(G, lcg(&G.rl[i]), &C->ri_moved[par], K);
+        const int nri = lcg(&C->rhcnt);
+        for (int w = gwarp; w < nri; w += nwarps) {
+            const int2 item = lcg(&G.hri[w]);
+            const int u = item.x;
             const int hu = lcg(&G.h[u]);
             const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
-            const long long moved = warp_sum(remove_invalid_range(G, hu, item.y, a1, K));
+            const long long moved = warp_sum(remove_invalid_range(G, hu, item.y, a1, &C->ri_moved[par], K));
             if (lane == 0 && moved) add_ll(&G.e[u], -moved);
         }
-        MF_SYNC_T(S_T_RI, 0, 0, nrl);
+        MF_SYNC_T(S_T_RI, 0, 0, nrl + nri);
+
+        // Alg. 4's loop test, on the heights PushRelabel left: no vertex is
+        // active if every activation was served (the last round's list is
+        // empty, no hub is left active or was turned active again) and
+        // RemoveInvalidEdges moved nothing.  The labelling is then valid (the
+        // only arcs that pushes and relabels can make steep leave relabelled
+        // vertices, and RemoveInvalidEdges found none), so each vertex with
+        // excess sits at height >= n and cannot reach a sink: the preflow is
+        // maximum without another BFS.  The value needs the current deficits.
+        const int busy = (rounds_clean ? 0 : 1) | (hubs_clean ? 0 : 2) | (lcg(&C->ri_moved[par]) ? 4 : 0) |
+                         (pend > 0 ? 8 : 0);
+        if (gtid == 0 && TR && C->trace_n - 1 < G.trace_cap) TR[C->trace_n - 1].mode = (short)busy;
+        if (!J.exact_exit && kind != JOB_REFRESH && busy == 0) {
+            long long dsum = 0;
+            for (long long v = gtid; v < n; v += gthreads) {
+                const long long ev = lcg(&G.e[v]);
+                if (v != s && v != t && ev < 0) dsum += ev;
+            }
+            dsum = warp_sum(dsum);
+            if (lane == 0 && dsum) add_ll(&C->dacc[par ^ 1], dsum);
+            MF_SYNC_T(S_T_RESET, 1, 0, 0);
+            early = true;
+            break;
+        }
     }
 
     // ---- result and statistics -------------------------------------------
     if (gtid == 0) {
-        C->flow = lcg(&G.e[t]) + lcg(&C->dacc[it & 1]);
-        C->iters = it;
+        // dacc: deficits at the last height init, or recounted at a clean exit
+        if (!fast) C->flow = lcg(&G.e[t]) + lcg(&C->dacc[early ? (it & 1) ^ 1 : it & 1]);
+        if (kind != JOB_REFRESH) {
+            C->iters = fast ? 0 : early ? it + 1 : it;
+            C->exit_kind = fast ? EXIT_NO_CUT_CHANGE : early ? EXIT_CLEAN : EXIT_BFS;
+        }
+        C->heights_exact = !fast && !early;
+        C->cut_exact = !early;   // the fast path keeps the exact cut it started from
+        C->ri_moved[0] = C->ri_moved[1] = 0;
+        C->phc[0] = C->phc[1] = 0;
+        C->rhcnt = 0;
+        C->inc_block = 0;
         for (int i = 0; i < 3; ++i) {
             C->qcnt[i] = C->ccnt[i] = C->gtk[i] = C->ctk[i] = 0;
             C->asum[i] = 0;
@@ -1301,8 +1455,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         C->wcnt = C->hcnt = C->hccnt = C->rlcnt = 0;
         C->acnt[0] = C->acnt[1] = C->acnt[2] = 0;
         C->rtk[0] = C->rtk[1] = C->rtk[2] = 0;
-        C->stamp_base = stamp_base + (unsigned)(it + 1) * (kMaxRounds + 1);
-        if (kind != JOB_SOLVE) C->bseq = seq;
+        C->stamp_base = snext;
+        if (batch_job) C->bseq = seq;
         C->hub_act[0] = C->hub_act[1] = 0;
         C->hlc[0] = C->hlc[1] = 0;
         C->dacc[0] = C->dacc[1] = 0;
@@ -1314,9 +1468,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const long long v = warp_sum(vals[i]);
-        if (lane == 0 && v) add_ll(&C->st[idx[i]], v);
+        if (lane == 0 && v) add_ll(&ST[idx[i]], v);
     }
 }
+
+#undef ST
+#undef TR
 
 // ------------------------------------------------------------- policy --
 struct PolicyJob {
@@ -1464,10 +1621,12 @@ struct NoAllocLayout {
     static constexpr size_t hdone = hnit + align256(sizeof(int) * kNoAllocMaxHubs);
     static constexpr size_t hkey = hdone + align256(sizeof(int) * kNoAllocMaxHubs);
     static constexpr size_t hrem = hkey + align256(sizeof(unsigned long long) * kNoAllocMaxHubs);
-    static constexpr size_t total = hrem + align256(sizeof(long long) * kNoAllocMaxHubs);
+    static constexpr size_t hl2 = hrem + align256(sizeof(long long) * kNoAllocMaxHubs);
+    static constexpr size_t hri = hl2 + align256(sizeof(int) * kNoAllocMaxHubs);
+    static constexpr size_t total = hri + align256(sizeof(int2) * (kNoAllocMaxArcs / kPrChunk + kNoAllocMaxHubs));
 };
 
-static_assert(NoAllocLayout::total == 13353472, "the header states the scratch size (13,353,472 bytes)");
+static_assert(NoAllocLayout::total == 13533952, "the header states the scratch size (13,533,952 bytes)");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NoAllocLayout::total];
 
 }  // namespace mf
@@ -1592,6 +1751,8 @@ int read_ctl(mf_graph *g, Ctl *out, size_t bytes = sizeof(Ctl)) {
 int launch(mf_graph *g, const Job &job, cudaStream_t st) {
     DevGraph dg = g->dg;
     Job jb = job;
+    jb.st = job.kind == JOB_REFRESH ? g->dg.ctl->st_aux : g->dg.ctl->st;
+    jb.trace = job.kind == JOB_REFRESH ? nullptr : g->dg.trace;
     void *args[] = {&dg, &jb};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_solve, dim3(g->grid), dim3(kBlock), args, 0, st);
     if (e != cudaSuccess) {
@@ -1639,6 +1800,19 @@ int ensure_batch_capacity(mf_graph *g, int64_t k, cudaStream_t st) {
     }
     g->b_cap = want;
     return MF_OK;
+}
+
+// Make h the exact BFS heights of the current state (a no-op on the device
+// when they are exact already), on the graph's last stream.
+int refresh_heights(mf_graph *g) {
+    Job j{};
+    j.kind = JOB_REFRESH;
+    j.exact_exit = 1;
+    j.kc = g->kc;
+    j.mode = g->opt.mode;
+    j.max_iters = g->max_iters;
+    j.time_limit_ns = g->time_limit_ns;
+    return launch(g, j, g->last);
 }
 
 int status_to_code(mf_graph *g, const Ctl &c) {
@@ -1763,6 +1937,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     D.cb = dnew<int2>(g, size_t(std::max<int64_t>(H.chunk_items, 1)));
     const size_t NH = size_t(std::max<int64_t>(H.hubs, 1));
     D.hl = dnew<int>(g, NH);
+    D.hl2 = dnew<int>(g, NH);
     D.hmode = dnew<int>(g, NH);
     D.hkey = dnew<unsigned long long>(g, NH);
     D.hrem = dnew<long long>(g, NH);
@@ -1772,6 +1947,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     D.hlv0 = dnew<int2>(g, size_t(std::max<int64_t>(H.hub_chunk_items, 1)));
     D.hlv1 = dnew<int2>(g, size_t(std::max<int64_t>(H.hub_chunk_items, 1)));
     D.hikey = dnew<unsigned>(g, size_t(std::max<int64_t>(H.hub_chunk_items, 1)));
+    D.hri = dnew<int2>(g, size_t(std::max<int64_t>(H.hub_chunk_items, 1)));
     D.astamp = dnew<unsigned>(g, N);
     D.rstamp = dnew<unsigned>(g, N);
     D.rl = dnew<int>(g, N);
@@ -1779,7 +1955,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     g->side_buf = dnew<unsigned char>(g, N);
     if (!row || !head || !rev || !aoe || !D.cap || !D.r || !D.rr || !D.h || !D.e || !D.cap_edge || !D.stamp ||
         !D.qb0 || !D.qb1 || !D.wl || !D.cb || !D.ctl || !g->side_buf || !D.hl || !D.hmode || !D.hkey ||
-        !D.hrem || !D.hnit || !D.hdone || !D.hcl || !D.hlv0 || !D.hlv1 || !D.hikey || !D.astamp || !D.rstamp || !D.rl)
+        !D.hrem || !D.hnit || !D.hdone || !D.hcl || !D.hlv0 || !D.hlv1 || !D.hikey || !D.hl2 || !D.hri || !D.astamp || !D.rstamp || !D.rl)
         return fail(MF_ENOMEM, "device allocation failed");
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
@@ -1973,14 +2149,15 @@ int mf_min_cut(mf_graph *g, uint8_t *side, int32_t flags) {
     if (!g || !side) return MF_EINVAL;
     if (!g->solved) return set_err(MF_ENOTSOLVED, "call mf_solve first");
     MF_CUDA(cudaSetDevice(g->dev));
+    int rc = refresh_heights(g);
+    if (rc) return rc;
     unsigned char *dst = (flags & MF_DEVICE_PTRS) ? side : g->side_buf;
     int blocks = std::max(1, std::min(g->sms * 4, (g->n + 255) / 256));
     k_cut_side<<<blocks, 256, 0, g->last>>>(g->dg.h, g->n, dst);
     MF_CUDA(cudaGetLastError());
     if (!(flags & MF_DEVICE_PTRS))
         MF_CUDA(cudaMemcpyAsync(side, g->side_buf, size_t(g->n), cudaMemcpyDeviceToHost, g->last));
-    MF_CUDA(cudaStreamSynchronize(g->last));
-    return MF_OK;
+    return mf_sync(g);
 }
 
 int mf_stats_get(mf_graph *g, mf_stats *out) {
@@ -2019,6 +2196,7 @@ int mf_stats_get(mf_graph *g, mf_stats *out) {
     out->policy_kind = c.pol_kind == JOB_RECOMPUTE ? 1 : 0;
     out->policy_kernel_cycles = c.pol_kc;
     out->policy_fallback = c.pol_fallback;
+    out->exit_kind = c.exit_kind;
     out->status = c.status;
     out->kernel_cycles = g->kc;
     out->grid_blocks = g->grid;
@@ -2044,6 +2222,10 @@ int mf_export_graph(mf_graph *g, int64_t *arc_row, int32_t *head, int32_t *rev, 
 int mf_export_state(mf_graph *g, int32_t *r, int64_t *excess, int32_t *height, int32_t flags) {
     if (!g) return MF_EINVAL;
     MF_CUDA(cudaSetDevice(g->dev));
+    if (height && g->solved) {
+        int rc = refresh_heights(g);
+        if (rc) return rc;
+    }
     cudaMemcpyKind kind = (flags & MF_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (r && g->A) MF_CUDA(cudaMemcpyAsync(r, g->dg.r, size_t(g->A) * 4, kind, g->last));
     if (excess) MF_CUDA(cudaMemcpyAsync(excess, g->dg.e, size_t(g->n) * 8, kind, g->last));
@@ -2236,12 +2418,17 @@ int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const in
     D.hdone = reinterpret_cast<int *>(b + Lo::hdone);
     D.hkey = reinterpret_cast<unsigned long long *>(b + Lo::hkey);
     D.hrem = reinterpret_cast<long long *>(b + Lo::hrem);
+    D.hl2 = reinterpret_cast<int *>(b + Lo::hl2);
+    D.hri = reinterpret_cast<int2 *>(b + Lo::hri);
     // the previous call's contents stay in the array: clear what must start at 0
     MF_CUDA(cudaMemsetAsync(D.ctl, 0, sizeof(Ctl), st));
     MF_CUDA(cudaMemsetAsync(D.astamp, 0, sizeof(unsigned) * size_t(n), st));
     MF_CUDA(cudaMemsetAsync(D.rstamp, 0, sizeof(unsigned) * size_t(n), st));
     Job j{};
     j.kind = JOB_SOLVE;
+    j.exact_exit = 1;   // the caller reads the cut {height >= n} from the heights
+    j.st = D.ctl->st;
+    j.trace = nullptr;
     j.kc = kernel_cycles > 0 ? kernel_cycles : int(std::max<int64_t>(1, (arcs / 2 + n / 2) / n));
     j.max_iters = 4LL * n + 1000;
     j.time_limit_ns = 60ull * 1000ull * 1000ull * 1000ull;

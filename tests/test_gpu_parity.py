@@ -225,7 +225,9 @@ def test_rejected_batches_leave_state_unchanged(mf):
 
 
 def test_iteration_cap_reports_timeout_and_solve_recovers(mf):
-    g = gen.rmat(scale=12, seed=3)
+    # a segmentation grid: its static solve starts with every pixel active,
+    # far more than one activation-round cap can finish in one iteration
+    g = gen.grid_segmentation(256, 192, seed=3)
     cap = g.cap.copy()
     G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t, max_iters=1)
     G.solve()
@@ -348,4 +350,80 @@ def test_full_size_grid4096_rect_batches(mf):
         for i in range(2):
             yield gen.grid_rect_batch(g, seed=3, index=i)
     G, _ = run_batches(mf, g, batches, kernel_cycles=4)
+    G.close()
+
+
+def test_clean_exit_without_final_bfs(mf):
+    """When the last PushRelabel/RemoveInvalidEdges round leaves no active
+    vertex the loop stops without another BFS (exit_kind 1; on the
+    segmentation grid, whose few high-degree vertices are s and t, this is
+    the common case).  Every value still equals the oracle's, and the
+    certificate (which asks for the cut and exact heights, recomputed by one
+    BFS) holds."""
+    kinds = {}
+    cases = (("grid", gen.grid_segmentation(256, 192, seed=45)), ("rmat", gen.rmat(scale=13, seed=44)))
+    for name, g in cases:
+        cap = g.cap.copy()
+        G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t)
+        G.solve()
+        kinds[name] = [G.stats()["exit_kind"]]
+        for i in range(5):
+            if name == "grid":
+                b = gen.grid_rect_batch(g, seed=45, index=i, side_lo=16, side_hi=96)
+            else:
+                b = gen.mixed_batch(cap, max(10, g.m // (100 if i % 2 else 1000)), 1, 500, seed=44, index=i)
+            G.apply_updates(b.edge_id, b.new_cap)
+            gen.apply_batch(cap, b)
+            f = G.flow_value()
+            st = G.stats()
+            kinds[name].append(st["exit_kind"])
+            assert f == oracle_flow(g, cap)
+            if st["exit_kind"] == 1 or i == 4:
+                certify_gpu(G, g, cap, f)
+        G.close()
+    assert set(kinds["grid"] + kinds["rmat"]) <= {0, 1}, kinds
+    assert 1 in kinds["grid"], kinds
+
+
+def test_pure_increment_fast_path(mf):
+    """A batch that only raises capacities of arcs not going from S to T of
+    the exact cut cannot change the flow value: no loop runs (exit_kind 2),
+    the value is the oracle's, the state stays certified; an increment on an
+    arc across the cut or any decrement takes the full repair."""
+    g = gen.rmat(scale=12, seed=41)
+    cap = g.cap.copy()
+    G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t)
+    G.solve()
+    f0 = G.flow_value()
+    side = G.min_cut()   # exact cut: recomputed by a BFS if needed
+    tails = g.tails()
+    crossing = (side[tails] == 1) & (side[g.col] == 0)
+    rng = np.random.default_rng(41)
+    off = np.flatnonzero(~crossing)
+    for rep in range(2):
+        ids = np.sort(rng.choice(off, 300, replace=False)).astype(np.int32)
+        new = (cap[ids].astype(np.int64) + rng.integers(1, 100, ids.size)).astype(np.int32)
+        G.apply_updates(ids, new)
+        cap[ids] = new
+        assert G.flow_value() == f0 == oracle_flow(g, cap)
+        st = G.stats()
+        assert st["exit_kind"] == 2 and st["bfs_levels"] == 0 and st["iterations"] == 0
+    certify_gpu(G, g, cap, f0)
+    xs = np.flatnonzero(crossing)
+    assert xs.size > 0
+    ids = xs[:4].astype(np.int32)
+    new = (cap[ids].astype(np.int64) + 50).astype(np.int32)
+    G.apply_updates(ids, new)
+    cap[ids] = new
+    f1 = G.flow_value()
+    assert G.stats()["exit_kind"] != 2 and f1 == oracle_flow(g, cap) and f1 >= f0
+    G.min_cut()
+    ids = np.sort(rng.choice(off, 50, replace=False)).astype(np.int32)
+    new = cap[ids].copy()
+    new[np.flatnonzero(new > 0)[0]] -= 1      # one decrement among unchanged entries
+    G.apply_updates(ids, new)
+    cap[ids] = new
+    assert G.flow_value() == oracle_flow(g, cap)
+    assert G.stats()["exit_kind"] != 2
+    certify_gpu(G, g, cap, G.flow_value())
     G.close()

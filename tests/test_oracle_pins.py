@@ -281,6 +281,41 @@ def test_update_monotonicity_bounds():
     assert oracle.maxflow_fifo(g.n, g.row_ptr, g.col, down, g.s, g.t) <= f_old
 
 
+def test_increments_off_the_min_cut_leave_the_value():
+    """Raising capacities of edges that do not go from S to T of a minimum cut
+    (S = vertices that cannot reach t in the final residual graph, found here
+    by scipy's BFS) leaves the maximum flow unchanged; raising one edge that
+    does cross can raise it, never by more than the increment."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import breadth_first_order
+    for seed in range(4):
+        g = gen.rmat(scale=9, seed=300 + seed)
+        cap = g.cap.copy()
+        f, st = oracle.maxflow_fifo(g.n, g.row_ptr, g.col, cap, g.s, g.t, want_state=True)
+        tails = np.repeat(np.arange(g.n), np.diff(st.arc_row))
+        res = st.r > 0
+        # reverse residual graph: who can reach t
+        R = csr_matrix((np.ones(int(res.sum())), (st.head[res], tails[res])), shape=(g.n, g.n))
+        reach = np.zeros(g.n, bool)
+        reach[breadth_first_order(R, g.t, directed=True, return_predecessors=False)] = True
+        S = ~reach
+        assert S[g.s] and not S[g.t]
+        et = g.tails()
+        crossing = S[et] & ~S[g.col]
+        assert int(cap[crossing].astype(np.int64).sum()) == f      # it is a minimum cut
+        rng = np.random.default_rng(seed)
+        up = cap.copy()
+        off = np.flatnonzero(~crossing)
+        pick = rng.choice(off, min(200, off.size), replace=False)
+        up[pick] += rng.integers(1, 1000, pick.size).astype(np.int32)
+        assert oracle.maxflow_fifo(g.n, g.row_ptr, g.col, up, g.s, g.t) == f
+        e = np.flatnonzero(crossing)[0]
+        up = cap.copy()
+        up[e] += 7
+        f2 = oracle.maxflow_fifo(g.n, g.row_ptr, g.col, up, g.s, g.t)
+        assert f <= f2 <= f + 7
+
+
 # ---- the policy network oracle -------------------------------------------
 from oracle import mlp as omlp  # noqa: E402
 
