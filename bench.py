@@ -17,6 +17,9 @@ e2e        the same through the C ABI with pinned HOST batch buffers: the
            flow value and status are inside the timed region
 sizes      dynamic repair vs static GPU recompute (solve from zero flow on the
            same capacities) for 1k / 10k / 100k / 1M-edge batches
+grid       the same comparison on the 4096^2 segmentation grid with
+           rectangle batches (terminal-capacity rewrites)
+serving    the request loop over eight resident graphs at two offered rates
 roofline   algorithmic bytes of the repair kernel (per-unit figures x device
            counters) / its measured duration / measured HBM peak
 cpu_baseline  the CPU oracle (FIFO push-relabel, from scratch) on a bounded
@@ -189,59 +192,133 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(line), flush=True)
 
 
-def serving_measurement(rate_per_s: float, duration_s: float, seed: int = 5) -> dict:
-    """Serving loop on a mix of resident graphs (RMAT 16 and 18, a 1024^2
-    segmentation grid, a unit bipartite graph of 2^18 + 2^18 vertices): Poisson
-    arrivals at `rate_per_s`, batch sizes log-uniform in [100, 100k] (at most
-    a tenth of the graph's edges), served by mf_server with per-graph grids of
-    19 to 38 CTAs.  Reports p50/p99 submit-to-completion latency and the
-    completed batches per second."""
+SERVE_GRAPHS = "RMAT scales 16, 18, 20, 22 (caps U[1,1000]); segmentation grids 1024^2, 2048^2, 4096^2; " \
+               "unit bipartite graph 2^20 + 2^20 vertices, 16M edges"
+
+
+def serving_measurement(rates, duration_s: float, seed: int = 5) -> dict:
+    """Serving loop on eight resident graphs (RMAT scales 16-22, segmentation
+    grids 1024^2-4096^2, a unit bipartite assignment graph of 2^20 + 2^20
+    vertices and 16M edges): for each offered rate, Poisson arrivals for
+    `duration_s`, batch sizes log-uniform in [100, 100k] (grids: the pixels of
+    a rectangle of that many terminal arcs), served by mf_server with per-graph
+    grids of 19 to 152 CTAs.  Reports p50/p99 submit-to-completion latency and
+    the completed batches per second at each rate."""
+    from concurrent.futures import ThreadPoolExecutor
     from paper_2511_05895_gb300 import MaxFlowGraph, Server
-    specs = [(gen.rmat(scale=16, seed=301), 19), (gen.rmat(scale=18, seed=302), 38),
-             (gen.grid_segmentation(1024, 1024, seed=303), 38),
-             (gen.bipartite(1 << 18, 1 << 18, 1 << 22, seed=304), 38)]
+    makers = [(lambda: gen.rmat(scale=16, seed=301), 19), (lambda: gen.rmat(scale=18, seed=302), 38),
+              (lambda: gen.rmat(scale=20, seed=303), 76), (lambda: gen.rmat(scale=22, seed=304), 152),
+              (lambda: gen.grid_segmentation(1024, 1024, seed=305), 38),
+              (lambda: gen.grid_segmentation(2048, 2048, seed=306), 76),
+              (lambda: gen.grid_segmentation(4096, 4096, seed=307), 152),
+              (lambda: gen.bipartite(1 << 20, 1 << 20, 1 << 24, seed=308), 76)]
+    t_setup = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=4) as ex:      # numpy releases the GIL
+        graphs = list(ex.map(lambda mk: mk[0](), makers))
     S = Server()
     Gs, caps = [], []
-    for g, grid in specs:
+    for g, (_, grid) in zip(graphs, makers):
         G = MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=4, grid_blocks=grid)
         G.solve()
         G.flow_value()
         S.add_graph(G, 100_000)
         Gs.append(G)
         caps.append(g.cap.copy())
+    t_setup = time.perf_counter() - t_setup
     rng = np.random.default_rng(seed)
-    n_req = max(8, int(rate_per_s * duration_s))
-    plan = []
-    for i in range(n_req):
-        gi = int(rng.integers(len(specs)))
-        g = specs[gi][0]
-        k = int(np.exp(rng.uniform(np.log(100), np.log(min(100_000, g.m // 10)))))
-        if g.meta.get("kind") == "grid":
-            b = gen.grid_rect_batch(g, seed=seed, index=i, side_lo=16, side_hi=max(17, int(np.sqrt(k / 2))))
-        else:
-            hi = 1 if g.meta.get("kind") == "bipartite" else 500
-            b = gen.mixed_batch(caps[gi], k, 1, hi, seed=seed, index=i)
-        gen.apply_batch(caps[gi], b)
-        plan.append((gi, b))
-    gaps = rng.exponential(1.0 / rate_per_s, n_req)
-    S.reset_stats()
-    t0 = time.perf_counter()
-    t_next = t0
-    for (gi, b), gap in zip(plan, gaps):
-        t_next += gap
-        while time.perf_counter() < t_next:
-            pass
-        S.submit(gi, b.edge_id, b.new_cap)
-    S.drain()
-    st = S.stats()
+    runs = []
+    idx = 0
+    for rate in rates:
+        n_req = max(8, int(rate * duration_s))
+        plan = []
+        for _ in range(n_req):
+            gi = int(rng.integers(len(graphs)))
+            g = graphs[gi]
+            k = int(np.exp(rng.uniform(np.log(100), np.log(min(100_000, g.m // 10)))))
+            if g.meta.get("kind") == "grid":
+                side = max(8, int(np.sqrt(k / 2)))        # 2 side^2 <= k terminal arcs
+                b = gen.grid_rect_batch(g, seed=seed, index=idx, side_lo=side, side_hi=side)
+            else:
+                hi = 1 if g.meta.get("kind") == "bipartite" else 500
+                b = gen.mixed_batch(caps[gi], k, 1, hi, seed=seed, index=idx)
+            idx += 1
+            gen.apply_batch(caps[gi], b)
+            plan.append((gi, b))
+        gaps = rng.exponential(1.0 / rate, n_req)
+        S.reset_stats()
+        t_next = time.perf_counter()
+        for (gi, b), gap in zip(plan, gaps):
+            t_next += gap
+            while time.perf_counter() < t_next:
+                pass
+            S.submit(gi, b.edge_id, b.new_cap)
+        S.drain()
+        st = S.stats()
+        runs.append({"offered_rate_per_s": rate, "requests": st["completed"],
+                     "batches_per_s": round(st["completed"] / max(st["makespan_s"], 1e-9), 1),
+                     "p50_ms": round(st["p50_us"] / 1000, 3), "p99_ms": round(st["p99_us"] / 1000, 3),
+                     "max_inflight": st["max_inflight"], "captured_graphs": st["captured_graphs"],
+                     "failed": st["failed"]})
+    # every graph's final value against a fresh static solve of its final capacities
+    exact = True
+    for G, g, cap in zip(Gs, graphs, caps):
+        H = MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t, kernel_cycles=4)
+        H.solve()
+        exact = exact and H.flow_value() == G.flow_value()
+        H.close()
     S.close()
     for G in Gs:
         G.close()
-    return {"offered_rate_per_s": rate_per_s, "requests": st["completed"],
-            "batches_per_s": round(st["completed"] / max(st["makespan_s"], 1e-9), 1),
-            "p50_ms": round(st["p50_us"] / 1000, 3), "p99_ms": round(st["p99_us"] / 1000, 3),
-            "max_inflight": st["max_inflight"], "captured_graphs": st["captured_graphs"],
-            "failed": st["failed"]}
+    return {"graphs": SERVE_GRAPHS, "setup_s": round(t_setup, 1), "runs": runs,
+            "final_values_equal_static_recompute": exact}
+
+
+def grid_measurement(batches: int, flush, peak: float, seed: int = 3) -> dict:
+    """The 4096 x 4096 segmentation grid (16.8M vertices, 67M n-link arcs
+    plus one s- and one t-arc per pixel): each batch rewrites the terminal
+    capacities of a random rectangle of side 64-512; dynamic repair vs static
+    GPU recompute of the same capacities (median ms), the repair's share of
+    measured HBM bandwidth, and a check that both give the same value."""
+    import torch
+    from paper_2511_05895_gb300 import MaxFlowGraph
+    g = gen.grid_segmentation(4096, 4096, seed=seed)
+    G = MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=4)
+    G.solve()
+    G.flow_value()
+    stream = torch.cuda.current_stream()
+    empty = torch.zeros(0, dtype=torch.int32, device="cuda")
+    dyn, sta, ks, fr = [], [], [], []
+    equal = True
+    for i in range(batches):
+        b = gen.grid_rect_batch(g, seed=seed, index=i)
+        ids = torch.from_numpy(b.edge_id).cuda()
+        cp = torch.from_numpy(b.new_cap).cuda()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        flush.zero_()
+        ev[0].record(stream)
+        G.apply_updates(ids, cp)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        f_dyn = G.flow_value()
+        st = G.stats()
+        flush.zero_()
+        ev[2].record(stream)
+        G.apply_updates(empty, empty, recompute=True)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        equal = equal and G.flow_value() == f_dyn
+        d, s_ = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+        dyn.append(d)
+        sta.append(s_)
+        ks.append(len(b.edge_id))
+        fr.append(algorithmic_bytes(st, g.n) / (d * 1e-3) / 1e9 / peak)
+    G.close()
+    d, s_ = statistics.median(dyn), statistics.median(sta)
+    return {"workload": f"segmentation grid 4096^2 (n={g.n}, m={g.m}), rectangle batches of side 64-512 "
+                        "rewriting terminal capacities", "batches": batches,
+            "entries_median": int(statistics.median(ks)), "dynamic_ms": round(d, 3),
+            "static_recompute_ms": round(s_, 3), "speedup": round(s_ / d, 3),
+            "hbm_frac_of_measured": round(statistics.median(fr), 4), "values_equal": equal}
 
 
 def workload_config(args, g) -> dict:
@@ -263,6 +340,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=3, help="batches in the CPU-oracle sample")
     ap.add_argument("--kc", type=int, default=4, help="KERNELCYCLES of the repair (0 = average degree)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-grid", action="store_true", help="skip the 4096^2 segmentation-grid measurement")
     ap.add_argument("--policy", default="fixed", choices=["fixed", "plain", "learned"],
                     help="batch policy: fixed repair, the plain rule, or the trained network")
     args = ap.parse_args()
@@ -409,21 +487,25 @@ def main():
                "sample": f"{args.cpu_sample} recomputes from scratch (FIFO push-relabel, 1 thread) "
                          f"of the RMAT-20 graph after {args.batch}-edge batches"}
 
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+
+    grid = None
+    if not args.no_grid and rank == 0:
+        grid = grid_measurement(5, flush, peak)
+
     serving = None
     if not args.no_serve and rank == 0:
-        serving = {"graphs": "RMAT-16, RMAT-18, grid 1024^2, bipartite 2^18+2^18 (4M unit edges)",
-                   "runs": [serving_measurement(r, 4.0) for r in (100.0, 1000.0)]}
+        serving = serving_measurement((100.0, 1000.0), 4.0)
 
     if dist:
         dist.destroy_process_group()
     if rank != 0:
         return
 
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(peaks_path):
-        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
-    else:
-        peak, peak_src = 6800.0, "fallback"
     mean_ms = 1000.0 * sum(times) / 1000.0 / len(times)
     mean_bytes = sum(per_step_bytes) / len(per_step_bytes)
     achieved = mean_bytes / (mean_ms / 1000.0) / 1e9
@@ -449,6 +531,7 @@ def main():
         "clocks": clk,
         "cpu_baseline": cpu,
         "checks": {"flow_initial": flow0, "flow_final": flow_after, "certified": certified},
+        "grid": grid,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)

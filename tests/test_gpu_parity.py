@@ -355,34 +355,41 @@ def test_full_size_grid4096_rect_batches(mf):
 
 def test_clean_exit_without_final_bfs(mf):
     """When the last PushRelabel/RemoveInvalidEdges round leaves no active
-    vertex the loop stops without another BFS (exit_kind 1; on the
-    segmentation grid, whose few high-degree vertices are s and t, this is
-    the common case).  Every value still equals the oracle's, and the
-    certificate (which asks for the cut and exact heights, recomputed by one
-    BFS) holds."""
-    kinds = {}
-    cases = (("grid", gen.grid_segmentation(256, 192, seed=45)), ("rmat", gen.rmat(scale=13, seed=44)))
+    vertex the loop stops without another BFS (exit_kind 1).  A path graph
+    does so deterministically (one iteration pushes everything to t); on the
+    larger workloads it depends on the schedule.  Every value still equals
+    the oracle's, and the certificate (which asks for the cut and exact
+    heights, recomputed by one BFS) holds."""
+    path = gen.from_edges(6, [0, 1, 2, 3, 4], [1, 2, 3, 4, 5], [9, 7, 8, 5, 6], 0, 5, name="path")
+    G = mf.MaxFlowGraph(path.n, path.row_ptr, path.col, path.cap, path.s, path.t)
+    G.solve()
+    assert G.flow_value() == 5 and G.stats()["exit_kind"] == 1
+    certify_gpu(G, path, path.cap.copy(), 5)
+    G.close()
+    kinds = []
+    cases = [("grid", gen.grid_segmentation(256, 192, seed=45)), ("rmat", gen.rmat(scale=13, seed=44))]
+    cases += [("random", gen.random_graph(seed=70 + i)) for i in range(4)]
     for name, g in cases:
         cap = g.cap.copy()
         G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t)
         G.solve()
-        kinds[name] = [G.stats()["exit_kind"]]
-        for i in range(5):
+        kinds.append(G.stats()["exit_kind"])
+        for i in range(4):
             if name == "grid":
                 b = gen.grid_rect_batch(g, seed=45, index=i, side_lo=16, side_hi=96)
             else:
-                b = gen.mixed_batch(cap, max(10, g.m // (100 if i % 2 else 1000)), 1, 500, seed=44, index=i)
+                b = gen.mixed_batch(cap, max(10, g.m // (100 if i % 2 else 1000)), 1, 50, seed=44, index=i)
             G.apply_updates(b.edge_id, b.new_cap)
             gen.apply_batch(cap, b)
             f = G.flow_value()
             st = G.stats()
-            kinds[name].append(st["exit_kind"])
+            kinds.append(st["exit_kind"])
             assert f == oracle_flow(g, cap)
-            if st["exit_kind"] == 1 or i == 4:
+            if st["exit_kind"] == 1 or i == 3:
                 certify_gpu(G, g, cap, f)
         G.close()
-    assert set(kinds["grid"] + kinds["rmat"]) <= {0, 1}, kinds
-    assert 1 in kinds["grid"], kinds
+    assert set(kinds) <= {0, 1}, kinds
+    print("exit kinds:", kinds)
 
 
 def test_pure_increment_fast_path(mf):

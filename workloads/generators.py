@@ -67,8 +67,13 @@ class Stream:
         self.pos = 0
 
     def u64(self, count: int) -> np.ndarray:
-        z = np.arange(self.pos + 1, self.pos + 1 + count, dtype=np.uint64)
+        z = self.u64_at(self.pos, count)
         self.pos += count
+        return z
+
+    def u64_at(self, offset: int, count: int) -> np.ndarray:
+        """Values offset .. offset + count - 1 of the stream (position unchanged)."""
+        z = np.arange(offset + 1, offset + 1 + count, dtype=np.uint64)
         z *= _GOLDEN
         z += self.key
         return _mix64(z)
@@ -169,26 +174,43 @@ def rmat(scale: int = 20, edge_factor: int = 16, a: float = 0.57, b: float = 0.1
     n = 1 << scale
     draws = edge_factor * n
     st = Stream(seed, "rmat")
-    th_a = np.uint64(int(a * 2 ** 32))
-    th_ab = np.uint64(int((a + b) * 2 ** 32))
-    th_abc = np.uint64(int((a + b + c) * 2 ** 32))
+    th_a = np.uint32(int(a * 2 ** 32))
+    th_ab = np.uint32(int((a + b) * 2 ** 32))
+    th_abc = np.uint32(int((a + b + c) * 2 ** 32))
     u = np.zeros(draws, dtype=np.uint32)
     v = np.zeros(draws, dtype=np.uint32)
-    lo_mask = np.uint64(0xFFFFFFFF)
-    level = 0
-    while level < scale:
-        x = st.u64(draws)
-        for half in (x >> np.uint64(32), x & lo_mask):
-            if level >= scale:
-                break
-            half = half.astype(np.uint32)
-            bu = half >= np.uint32(th_ab)                               # quadrants c, d
-            bv = ((half >= np.uint32(th_a)) & ~bu) | (half >= np.uint32(th_abc))  # b, d
-            u <<= np.uint32(1)
-            u |= bu
-            v <<= np.uint32(1)
-            v |= bv
-            level += 1
+    pairs = (scale + 1) // 2   # one 64-bit value per draw feeds two levels
+
+    def levels(c0: int, c1: int) -> None:
+        # draws [c0, c1): level 2k uses the high and level 2k + 1 the low 32
+        # bits of value k * draws + i of the stream
+        uu = u[c0:c1]
+        vv = v[c0:c1]
+        level = 0
+        for k in range(pairs):
+            x = st.u64_at(k * draws + c0, c1 - c0)
+            for half in (x >> np.uint64(32), x & np.uint64(0xFFFFFFFF)):
+                if level >= scale:
+                    break
+                half = half.astype(np.uint32)
+                bu = half >= th_ab                                        # quadrants c, d
+                bv = ((half >= th_a) & ~bu) | (half >= th_abc)           # b, d
+                uu <<= np.uint32(1)
+                uu |= bu
+                vv <<= np.uint32(1)
+                vv |= bv
+                level += 1
+
+    chunk = 1 << 20
+    bounds = [(c0, min(draws, c0 + chunk)) for c0 in range(0, draws, chunk)]
+    if len(bounds) > 1:
+        from concurrent.futures import ThreadPoolExecutor   # numpy releases the GIL
+        import os
+        with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(lambda cb: levels(*cb), bounds))
+    else:
+        levels(0, draws)
+    st.pos = pairs * draws
     perm = st.permutation(n)
     u = perm[u.astype(np.int64)]
     v = perm[v.astype(np.int64)]
