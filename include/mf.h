@@ -66,6 +66,15 @@ extern "C" {
 #define MF_MODE_DATA_DRIVEN 0  /* worklist of active vertices (Sec. 5.3)         */
 #define MF_MODE_TOPOLOGY    1  /* the first push/relabel round of each iteration
                                   visits every vertex id (Sec. 5.2)            */
+#define MF_MODE_PUSH_PULL   2  /* repairs by Dynamic Push-Pull (Alg. 8, Sec. 4.2):
+                                  saturate the arcs across the previous cut,
+                                  push on its sink side and pull on its source
+                                  side concurrently, then push on the leftover
+                                  subgraph P.  Needs the exact cut of the
+                                  previous state (after mf_solve, a BFS-ended or
+                                  push-pull repair); otherwise that repair runs
+                                  the plain dynamic loop.  exit_kind 3 marks a
+                                  push-pull repair.                            */
 
 typedef struct mf_graph mf_graph;
 
@@ -73,7 +82,8 @@ typedef struct mf_graph mf_graph;
  *  kernel_cycles  KERNELCYCLES of Algorithm 2: push/relabel steps per active
  *                 vertex between two global relabels.  0 = max(1, round(m/n)),
  *                 the average degree used in Sec. 6.1.
- *  mode           MF_MODE_DATA_DRIVEN (default) or MF_MODE_TOPOLOGY.
+ *  mode           MF_MODE_DATA_DRIVEN (default), MF_MODE_TOPOLOGY or
+ *                 MF_MODE_PUSH_PULL.
  *  max_iters      cap on loop iterations (one BFS + PushRelabel +
  *                 RemoveInvalidEdges round) of one solve or repair; reaching
  *                 it reports MF_ETIMEOUT.  0 = 4 * n + 1000.
@@ -123,9 +133,10 @@ typedef struct mf_options {
  *               vertex under its own (valid) heights, so no final BFS ran;
  *               2 = the batch only raised capacities of arcs that do not
  *               cross the last exact cut, so the flow value cannot change
- *               and no loop ran.  After 1 or 2 the heights are not the BFS
- *               fixed point; mf_min_cut and mf_export_state recompute them
- *               first (one BFS). */
+ *               and no loop ran; 3 = a Dynamic Push-Pull repair
+ *               (MF_MODE_PUSH_PULL).  After 1, 2 or 3 the heights are not the
+ *               BFS fixed point; mf_min_cut and mf_export_state recompute
+ *               them first (one BFS). */
 typedef struct mf_stats {
     int64_t flow;
     int64_t iterations;

@@ -16,7 +16,7 @@ from . import _build
 MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_ENOTSOLVED, MF_ETIMEOUT = range(6)
 MF_HOST_PTRS, MF_DEVICE_PTRS, MF_DELTA, MF_RECOMPUTE = 0x0, 0x1, 0x2, 0x4
 MF_POLICY_FIXED, MF_POLICY_PLAIN, MF_POLICY_LEARNED = 0, 1, 2
-MF_MODE_DATA_DRIVEN, MF_MODE_TOPOLOGY = 0, 1
+MF_MODE_DATA_DRIVEN, MF_MODE_TOPOLOGY, MF_MODE_PUSH_PULL = 0, 1, 2
 
 ERROR_NAMES = {MF_EINVAL: "MF_EINVAL", MF_ENOMEM: "MF_ENOMEM", MF_ECUDA: "MF_ECUDA",
                MF_ENOTSOLVED: "MF_ENOTSOLVED", MF_ETIMEOUT: "MF_ETIMEOUT"}

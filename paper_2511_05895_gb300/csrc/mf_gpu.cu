@@ -57,7 +57,7 @@ constexpr int ST_STICKY = ST_ITERS | ST_WAIT | ST_TIME;
 enum JobKind { JOB_SOLVE = 0, JOB_REPAIR = 1, JOB_RECOMPUTE = 2, JOB_AUTO = 3, JOB_REFRESH = 4 };
 
 // How the last solve/repair ended (mf_stats.exit_kind)
-enum ExitKind { EXIT_BFS = 0, EXIT_CLEAN = 1, EXIT_NO_CUT_CHANGE = 2 };
+enum ExitKind { EXIT_BFS = 0, EXIT_CLEAN = 1, EXIT_NO_CUT_CHANGE = 2, EXIT_PUSH_PULL = 3 };
 
 // Fewest PushRelabel activation rounds per loop iteration, and the fewest
 // cooperative cycles the high-degree vertices get per iteration (see k_solve).
@@ -157,12 +157,18 @@ struct DevGraph {
     unsigned *astamp;         // per-vertex stamp of the last activation list joined
     unsigned *rstamp;         // per-vertex stamp of the last relabel list joined
     int *rl;                  // vertices relabelled in the current loop iteration
+    unsigned char *part;      // push-pull partition per vertex (kPartT / kPartS / kPartP), or null
     Ctl *ctl;
 };
+
+// Push-pull partitions (Alg. 8): T can reach a sink, S cannot (the previous
+// cut); P holds what neither stage-1 BFS reached.
+constexpr unsigned char kPartT = 0, kPartS = 1, kPartP = 2;
 
 struct Job {
     int kind, k, flags, kc, mode;
     int exact_exit;      // 1: stop only after a BFS finds no active vertex
+    int pp;              // 1: a repair by Dynamic Push-Pull (Alg. 8) when the cut is exact
     long long *st;       // statistics array (Ctl::st, or Ctl::st_aux for JOB_REFRESH)
     TraceRec *trace;     // trace records, or nullptr
     const int *k_dev;    // if set, the batch size is read from device memory
@@ -318,7 +324,8 @@ __device__ __forceinline__ void warp_append_n(const bool (&pred)[kIlp], const in
 // bfs_discovered for kIlp slots per lane at once: the loads of all slots are
 // issued together and each list gets one reservation per warp.
 __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (&disc)[kIlp], const int (&v)[kIlp],
-                                                 int *ncnt, int *NF, long long *asum, Counters &K) {
+                                                 unsigned fwd, bool dual, int *ncnt, int *NF, long long *asum,
+                                                 Counters &K) {
     bool any = false;
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) any |= disc[j];
@@ -337,8 +344,9 @@ __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (
     for (int j = 0; j < kIlp; ++j) {
         ds += deg[j];
         K.bfs_verts += disc[j];
-        const bool act = disc[j] && ev[j] > 0;
-        hub[j] = act && deg[j] > kHubDeg;
+        // a vertex of the pull side (forward search) is active when deficient
+        const bool act = disc[j] && (((fwd >> j) & 1u) ? ev[j] < 0 : ev[j] > 0);
+        hub[j] = act && !dual && deg[j] > kHubDeg;
         small[j] = act && !hub[j];
     }
     ds = warp_sum(ds);
@@ -351,21 +359,22 @@ __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (
 // next frontier, its degree counts towards that frontier's arc total, and
 // with positive excess it is active: worklist (degree <= kHubDeg) or hub
 // list.  All 32 lanes call.
-__device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int v, int *ncnt, int *NF,
-                                               long long *asum, Counters &K) {
+__device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int v, bool fwd, bool dual,
+                                               int *ncnt, int *NF, long long *asum, Counters &K) {
     warp_append(disc, v, ncnt, NF);
     if (!__ballot_sync(kFull, disc)) return;
     int deg = 0;
     bool act = false;
     if (disc) {
         deg = __ldg(&G.row[v + 1]) - __ldg(&G.row[v]);
-        act = lcg(&G.e[v]) > 0;
+        const long long ev = lcg(&G.e[v]);
+        act = fwd ? ev < 0 : ev > 0;
         ++K.bfs_verts;
     }
     const long long ds = warp_sum((long long)deg);
     if ((threadIdx.x & 31) == 0 && ds) add_ll(asum, ds);
     if (__ballot_sync(kFull, act)) {
-        const bool hub = act && deg > kHubDeg;
+        const bool hub = act && !dual && deg > kHubDeg;
         warp_append(act && !hub, v, &G.ctl->wcnt, G.wl);
         warp_append(hub, v, &G.ctl->hcnt, G.hl);
     }
@@ -375,31 +384,36 @@ __device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int
 // v; ok[j] marks a real arc): the arc v -> u is residual iff rr[a] > 0; an
 // unvisited v (height n) gets height L + 1 (global relabel, Sec. 2.2).  Newly
 // reached vertices with positive excess are active and join the worklist
-// (degree <= kHubDeg) or the hub list.  Every load of a round is issued before
-// any of them is used.  All 32 lanes call.
+// (degree <= kHubDeg) or the hub list.  Slots whose bit is set in fwd belong
+// to the pull side of a push-pull repair and search forward instead: u -> v
+// residual (r[a] > 0), and a deficient v is active.  Every load of a round is
+// issued before any of them is used.  All 32 lanes call.
 __device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kIlp], const bool (&ok)[kIlp],
-                                            int L, int *ncnt, int *NF, long long *asum, Counters &K) {
+                                            unsigned fwd, bool dual, int L, int *ncnt, int *NF, long long *asum,
+                                            Counters &K) {
     const int n = G.n;
     int v[kIlp], rin[kIlp], hv[kIlp];
     bool disc[kIlp];
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) {
         v[j] = ok[j] ? __ldg(&G.head[a[j]]) : 0;
-        rin[j] = ok[j] ? lcg(&G.rr[a[j]]) : 0;
+        rin[j] = ok[j] ? lcg(((fwd >> j) & 1u) ? &G.r[a[j]] : &G.rr[a[j]]) : 0;
         K.bfs_arcs += ok[j];
     }
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) hv[j] = (rin[j] > 0 && v[j] != G.s) ? lcg(&G.h[v[j]]) : -1;
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) disc[j] = hv[j] == n && atomicCAS(&G.h[v[j]], n, L + 1) == n;
-    bfs_discovered_n(G, disc, v, ncnt, NF, asum, K);
+    bfs_discovered_n(G, disc, v, fwd, dual, ncnt, NF, asum, K);
 }
 
 // Expand up to 32 frontier vertices (one per lane, degree deg starting at
-// arc beg) with the arcs balanced over the lanes: lane i handles arcs
-// k0 + 32 j + i of the concatenated lists.
-__device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int deg, int L,
+// arc beg, fwd for the pull side of a push-pull repair) with the arcs
+// balanced over the lanes: lane i handles arcs k0 + 32 j + i of the
+// concatenated lists.
+__device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int deg, bool fwd, bool dual, int L,
                                                 int *ncnt, int *NF, long long *asum, Counters &K) {
+    const unsigned fwd_lanes = __ballot_sync(kFull, fwd);
     const int lane = threadIdx.x & 31;
     int incl = deg;
 #pragma unroll
@@ -412,6 +426,7 @@ __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int 
     for (int k0 = 0; k0 < total; k0 += 32 * kIlp) {
         int a[kIlp];
         bool ok[kIlp];
+        unsigned fw = 0;
 #pragma unroll
         for (int jj = 0; jj < kIlp; ++jj) {
             const int k = k0 + 32 * jj + lane;
@@ -426,8 +441,9 @@ __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int 
             const int oe = __shfl_sync(kFull, excl, j);
             ok[jj] = k < total;
             a[jj] = ob + (k - oe);
+            fw |= ((fwd_lanes >> j) & 1u) << jj;
         }
-        bfs_visit_n(G, a, ok, L, ncnt, NF, asum, K);
+        bfs_visit_n(G, a, ok, fw, dual, L, ncnt, NF, asum, K);
     }
 }
 
@@ -436,13 +452,17 @@ __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int 
 // arc v -> w into the current frontier (h(w) == L); the first one found gives
 // h(v) = L + 1.  The group's arcs are balanced over the lanes and the scan of
 // a vertex stops once it is found.  Vertices of degree > kBigDeg become
-// kChunk-arc items of the chunk list instead.  All 32 lanes call.
-__device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base, int L, int *ncnt, int *NF,
-                                                    long long *asum, int *ccnt, Counters &K) {
+// kChunk-arc items of the chunk list instead.  In the first stage of a
+// push-pull repair (dual) a vertex of the pull side looks for a residual arc
+// w -> v from the frontier instead, and only frontier vertices of the
+// vertex's own side count.  All 32 lanes call.
+__device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base, bool dual, int L, int *ncnt,
+                                                    int *NF, long long *asum, int *ccnt, Counters &K) {
     const int lane = threadIdx.x & 31;
     const int n = G.n;
     const int v = base + lane;
     int beg = 0, deg = 0;
+    const int side = (dual && v < n) ? G.part[v] : kPartT;
     if (v < n && v != G.s && lcg(&G.h[v]) == n) {
         beg = __ldg(&G.row[v]);
         deg = __ldg(&G.row[v + 1]) - beg;
@@ -464,6 +484,7 @@ __device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base,
         }
         const int total = __shfl_sync(kFull, incl, 31);
         const int excl = incl - deg;
+        const unsigned pull_lanes = __ballot_sync(kFull, side == kPartS);
         for (int k0 = 0; k0 < total && found != want; k0 += 32 * kIlp) {
             int a[kIlp], own[kIlp], ra[kIlp], w[kIlp];
 #pragma unroll
@@ -479,28 +500,31 @@ __device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base,
                 own[jj] = j;
                 a[jj] = __shfl_sync(kFull, beg, j) + (k - __shfl_sync(kFull, excl, j));
                 const bool live = k < total && !((found >> j) & 1u);
-                ra[jj] = live ? lcg(&G.r[a[jj]]) : 0;
+                ra[jj] = live ? lcg(((pull_lanes >> j) & 1u) ? &G.rr[a[jj]] : &G.r[a[jj]]) : 0;
                 w[jj] = live ? __ldg(&G.head[a[jj]]) : 0;
                 K.bfs_arcs += live;
             }
             unsigned hit = 0;
 #pragma unroll
             for (int jj = 0; jj < kIlp; ++jj)
-                if (ra[jj] > 0 && lcg(&G.h[w[jj]]) == L) hit |= 1u << own[jj];
+                if (ra[jj] > 0 && lcg(&G.h[w[jj]]) == L &&
+                    (!dual || G.part[w[jj]] == (((pull_lanes >> own[jj]) & 1u) ? kPartS : kPartT)))
+                    hit |= 1u << own[jj];
             found |= __reduce_or_sync(kFull, hit);
         }
     }
     const bool disc = (found >> lane) & 1u;
     if (disc) G.h[v] = L + 1;
-    bfs_discovered(G, disc, v, ncnt, NF, asum, K);
+    bfs_discovered(G, disc, v, side == kPartS, dual, ncnt, NF, asum, K);
 }
 
 // Bottom-up scan of one kChunk-arc item of a high-degree unvisited vertex;
 // several items of one vertex may find a parent, the height CAS elects one.
-__device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item, int L, int *ncnt, int *NF,
-                                                   long long *asum, Counters &K) {
+__device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item, bool dual, int L, int *ncnt,
+                                                   int *NF, long long *asum, Counters &K) {
     const int lane = threadIdx.x & 31;
     const int v = item.x;
+    const int side = dual ? G.part[v] : kPartT;
     bool disc = false;
     if (lcg(&G.h[v]) == G.n) {
         const int a1 = min(item.y + kChunk, __ldg(&G.row[v + 1]));
@@ -511,19 +535,20 @@ __device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item,
 #pragma unroll
             for (int j = 0; j < kIlp; ++j) {
                 const int a = a0 + 32 * j + lane;
-                R.ra[j] = a < a1 ? lcg(&G.r[a]) : 0;
+                R.ra[j] = a < a1 ? lcg(side == kPartS ? &G.rr[a] : &G.r[a]) : 0;
                 R.w[j] = a < a1 ? __ldg(&G.head[a]) : 0;
                 K.bfs_arcs += a < a1;
             }
             bool mine = false;
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j) mine |= R.ra[j] > 0 && lcg(&G.h[R.w[j]]) == L;
+            for (int j = 0; j < kIlp; ++j)
+                mine |= R.ra[j] > 0 && lcg(&G.h[R.w[j]]) == L && (!dual || G.part[R.w[j]] == side);
             hit = __any_sync(kFull, mine);
         }
         if (hit && lane == 0) disc = atomicCAS(&G.h[v], G.n, L + 1) == G.n;
     }
     disc = __shfl_sync(kFull, disc, 0);
-    bfs_discovered(G, disc && lane == 0, v, ncnt, NF, asum, K);
+    bfs_discovered(G, disc && lane == 0, v, side == kPartS, dual, ncnt, NF, asum, K);
 }
 
 // ------------------------------------------------------ push / relabel --
@@ -538,6 +563,18 @@ __device__ __forceinline__ long long push_arc(const DevGraph &G, int a, int v, i
     return (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&G.e[v]), (unsigned long long)d);
 }
 
+// One pull of d units into u along arc a (u -> v) of u's list: the arc
+// v -> u loses d of residual and v loses d of excess (PullRelabel, Alg. 6);
+// the caller adds the total to e(u).  Returns e(v) before the pull.
+__device__ __forceinline__ long long pull_arc(const DevGraph &G, int a, int v, int d) {
+    const int b = __ldg(&G.rev[a]);
+    atomicSub(&G.r[b], d);
+    atomicSub(&G.rr[a], d);
+    atomicAdd(&G.r[a], d);
+    atomicAdd(&G.rr[b], d);
+    return (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&G.e[v]), (unsigned long long)(-(long long)d));
+}
+
 // Where the vertices that a push makes active go: the list of the next
 // activation round (see the PushRelabel phase of k_solve).  A vertex enters
 // one list at most once, by the stamp of that list.
@@ -549,6 +586,7 @@ struct ActList {
     int *hcnt;         // the next pass's hub list (high-degree vertices a push
     int *hlist;        //   turned active), its size and its stamp
     unsigned hstamp;
+    bool dual;         // first stage of a push-pull repair: no hub lists
 };
 
 // A vertex whose height PushRelabel raised joins the relabel list of the loop
@@ -559,16 +597,19 @@ __device__ __forceinline__ void note_relabel(const DevGraph &G, int u, unsigned 
     if (atomicExch(&G.rstamp[u], rstamp) != rstamp) G.rl[atomicAdd(&G.ctl->rlcnt, 1)] = u;
 }
 
-// A push of d units raised e(v) from `old`: if v turned active (excess
-// positive, below height n, not s or t) it joins the next activation round
-// when its degree is <= kHubDeg, else the hub list of the next PushRelabel
-// pass.  All 32 lanes call.
-__device__ __forceinline__ void note_activation(const DevGraph &G, bool pushed, int v, long long old, long long d,
-                                                const ActList &AL) {
+// A push of d units raised e(v) from `old` (a pull lowered it): if v turned
+// active (excess positive -- for a pull, negative -- below height n, not s or
+// t) it joins the next activation round when its degree is <= kHubDeg or in
+// the first stage of a push-pull repair, else the hub list of the next
+// PushRelabel pass.  All 32 lanes call.
+template <bool PULL>
+__device__ __forceinline__ void note_activation_t(const DevGraph &G, bool moved, int v, long long old, long long d,
+                                                  const ActList &AL) {
     bool add = false, add_hub = false;
-    if (pushed && old <= 0 && old + d > 0 && v != G.s && v != G.t) {
+    const bool turned = PULL ? (old >= 0 && old - d < 0) : (old <= 0 && old + d > 0);
+    if (moved && turned && v != G.s && v != G.t) {
         if (lcg(&G.h[v]) < G.n) {
-            if (__ldg(&G.row[v + 1]) - __ldg(&G.row[v]) <= kHubDeg)
+            if (AL.dual || __ldg(&G.row[v + 1]) - __ldg(&G.row[v]) <= kHubDeg)
                 add = atomicExch(&G.astamp[v], AL.stamp) != AL.stamp;
             else
                 add_hub = atomicExch(&G.astamp[v], AL.hstamp) != AL.hstamp;
@@ -578,6 +619,11 @@ __device__ __forceinline__ void note_activation(const DevGraph &G, bool pushed, 
     warp_append(add_hub, v, AL.hcnt, AL.hlist);
 }
 
+__device__ __forceinline__ void note_activation(const DevGraph &G, bool pushed, int v, long long old, long long d,
+                                                const ActList &AL) {
+    note_activation_t<false>(G, pushed, v, old, d, AL);
+}
+
 // One round of a warp's arc scan: lane i holds arcs a0 + 32 j + i (j < kIlp)
 // with their residual (0 past `end`), head and the head's height.  All loads
 // of the round are issued before any is used.
@@ -585,17 +631,31 @@ struct ArcRound {
     int ra[kIlp], v[kIlp], hv[kIlp];
 };
 
-__device__ __forceinline__ void load_round(const DevGraph &G, int a0, int end, ArcRound &R) {
+// The residual is that of the arc u -> head (push) or head -> u (pull, the
+// mirror rr).  With a partition array pt, an arc to a vertex of another part
+// counts as absent (push-pull: each side works on its own vertices only).
+template <bool PULL>
+__device__ __forceinline__ void load_round_t(const DevGraph &G, int a0, int end, ArcRound &R,
+                                             const unsigned char *pt, unsigned char side) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) {
         const int a = a0 + 32 * j + lane;
         const bool ok = a < end;
-        R.ra[j] = ok ? lcg(&G.r[a]) : 0;
+        R.ra[j] = ok ? lcg(PULL ? &G.rr[a] : &G.r[a]) : 0;
         R.v[j] = ok ? __ldg(&G.head[a]) : 0;
+    }
+    if (pt) {
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j)
+            if (R.ra[j] > 0 && pt[R.v[j]] != side) R.ra[j] = 0;
     }
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) R.hv[j] = R.ra[j] > 0 ? lcg(&G.h[R.v[j]]) : 0;
+}
+
+__device__ __forceinline__ void load_round(const DevGraph &G, int a0, int end, ArcRound &R) {
+    load_round_t<false>(G, a0, end, R, nullptr, 0);
 }
 
 __device__ __forceinline__ int round_arcs(int a0, int end) {
@@ -629,22 +689,34 @@ __device__ __forceinline__ unsigned long long round_min_key(const ArcRound &R, i
 // second pass over the arcs; otherwise it relabels u to h^ + 1.  A vertex
 // without residual arcs gets height n.  Only u's warp lowers r(u, .) and e(u);
 // other warps only raise them, so every amount pushed is available.
+// With PULL the same steps are Algorithm 6 (PullRelabel) on a deficient u:
+// residual arcs into u, pulls of min(-e, c_f) from the lowest of them.
 // Still active after its steps: u takes part in the next round as well.
-__device__ __forceinline__ void requeue_if_active(const DevGraph &G, int u, const ActList &AL) {
+template <bool PULL>
+__device__ __forceinline__ void requeue_if_active_t(const DevGraph &G, int u, const ActList &AL) {
     if ((threadIdx.x & 31) == 0) {
         const int hu = lcg(&G.h[u]);
-        if (hu < G.n && lcg(&G.e[u]) > 0 && atomicExch(&G.astamp[u], AL.stamp) != AL.stamp)
+        const long long eu = lcg(&G.e[u]);
+        if (hu < G.n && (PULL ? eu < 0 : eu > 0) && atomicExch(&G.astamp[u], AL.stamp) != AL.stamp)
             AL.list[atomicAdd(AL.cnt, 1)] = u;
     }
     __syncwarp();
+}
+
+// The amount moved along arc a (u -> v) in one step: a push or a pull.
+template <bool PULL>
+__device__ __forceinline__ long long move_arc(const DevGraph &G, int a, int v, int d) {
+    return PULL ? pull_arc(G, a, v, d) : push_arc(G, a, v, d);
 }
 
 // push_relabel_warp for a vertex whose arcs fit in one round (<= 32 kIlp):
 // the round loaded for the lowest-neighbour scan also serves the pushes (the
 // heights are the ones read once for the step, and u's own residuals can only
 // have grown since).
-__device__ __forceinline__ void push_relabel_small(const DevGraph &G, int u, int beg, int end, int kc,
-                                                   const ActList &AL, Counters &K) {
+template <bool PULL>
+__device__ __forceinline__ void push_relabel_small_t(const DevGraph &G, int u, int beg, int end, int kc,
+                                                     const ActList &AL, const unsigned char *pt, unsigned char side,
+                                                     Counters &K) {
     const int lane = threadIdx.x & 31;
     const int n = G.n;
     for (int c = 0; c < kc; ++c) {
@@ -656,9 +728,10 @@ __device__ __forceinline__ void push_relabel_small(const DevGraph &G, int u, int
         }
         hu = __shfl_sync(kFull, hu, 0);
         eu = __shfl_sync(kFull, eu, 0);
+        if (PULL) eu = -eu;   // the deficit to fill
         if (hu >= n || eu <= 0) break;
         ArcRound R;
-        load_round(G, beg, end, R);
+        load_round_t<PULL>(G, beg, end, R, pt, side);
         K.pr_arcs += round_arcs(beg, end);
         const unsigned long long best = warp_min(round_min_key(R, beg, beg));
         if (best == ~0ull) {
@@ -688,28 +761,29 @@ __device__ __forceinline__ void push_relabel_small(const DevGraph &G, int u, int
             d = d < 0 ? 0 : (d > ra ? ra : d);
             long long old = 0;
             if (d > 0) {
-                old = push_arc(G, beg + 32 * j + lane, R.v[j], (int)d);
+                old = move_arc<PULL>(G, beg + 32 * j + lane, R.v[j], (int)d);
                 sent += d;
                 ++K.push;
             }
-            note_activation(G, d > 0, R.v[j], old, d, AL);
+            note_activation_t<PULL>(G, d > 0, R.v[j], old, d, AL);
             const long long tot = __shfl_sync(kFull, incl, 31);
             rem -= tot < rem ? tot : rem;
         }
         sent = warp_sum(sent);
-        if (lane == 0 && sent) add_ll(&G.e[u], -sent);
+        if (lane == 0 && sent) add_ll(&G.e[u], PULL ? sent : -sent);
         __syncwarp();
     }
-    requeue_if_active(G, u, AL);
+    requeue_if_active_t<PULL>(G, u, AL);
 }
 
-__device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int kc, const ActList &AL,
-                                                  Counters &K) {
+template <bool PULL>
+__device__ __forceinline__ void push_relabel_warp_t(const DevGraph &G, int u, int kc, const ActList &AL,
+                                                    const unsigned char *pt, unsigned char side, Counters &K) {
     const int lane = threadIdx.x & 31;
     const int n = G.n;
     const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
     if (end - beg <= 32 * kIlp) {
-        push_relabel_small(G, u, beg, end, kc, AL, K);
+        push_relabel_small_t<PULL>(G, u, beg, end, kc, AL, pt, side, K);
         return;
     }
     for (int c = 0; c < kc; ++c) {
@@ -721,11 +795,12 @@ __device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int 
         }
         hu = __shfl_sync(kFull, hu, 0);
         eu = __shfl_sync(kFull, eu, 0);
+        if (PULL) eu = -eu;
         if (hu >= n || eu <= 0) break;
         unsigned long long best = ~0ull;
         for (int a0 = beg; a0 < end; a0 += 32 * kIlp) {
             ArcRound R;
-            load_round(G, a0, end, R);
+            load_round_t<PULL>(G, a0, end, R, pt, side);
             K.pr_arcs += round_arcs(a0, end);
             const unsigned long long k = round_min_key(R, a0, beg);
             best = k < best ? k : best;
@@ -752,7 +827,7 @@ __device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int 
         long long rem = eu, sent = 0;
         for (int a0 = beg; a0 < end && rem > 0; a0 += 32 * kIlp) {
             ArcRound R;
-            load_round(G, a0, end, R);
+            load_round_t<PULL>(G, a0, end, R, pt, side);
             K.pr_arcs += round_arcs(a0, end);
 #pragma unroll
             for (int j = 0; j < kIlp; ++j) {
@@ -762,37 +837,47 @@ __device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int 
                 d = d < 0 ? 0 : (d > ra ? ra : d);
                 long long old = 0;
                 if (d > 0) {
-                    old = push_arc(G, a0 + 32 * j + lane, R.v[j], (int)d);
+                    old = move_arc<PULL>(G, a0 + 32 * j + lane, R.v[j], (int)d);
                     sent += d;
                     ++K.push;
                 }
-                note_activation(G, d > 0, R.v[j], old, d, AL);
+                note_activation_t<PULL>(G, d > 0, R.v[j], old, d, AL);
                 const long long tot = __shfl_sync(kFull, incl, 31);
                 rem -= tot < rem ? tot : rem;
             }
         }
         sent = warp_sum(sent);
-        if (lane == 0 && sent) add_ll(&G.e[u], -sent);
+        if (lane == 0 && sent) add_ll(&G.e[u], PULL ? sent : -sent);
         __syncwarp();
     }
-    requeue_if_active(G, u, AL);
+    requeue_if_active_t<PULL>(G, u, AL);
+}
+
+__device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int kc, const ActList &AL,
+                                                  Counters &K) {
+    push_relabel_warp_t<false>(G, u, kc, AL, nullptr, 0, K);
 }
 
 // Algorithm 3 over the arcs [a0, a1) of vertex u (height hu) by one warp:
 // every residual arc u -> v with h(u) > h(v) + 1 is saturated, moving its
-// residual as excess to v.  Returns this lane's share of the excess moved.
-__device__ __forceinline__ long long remove_invalid_range(const DevGraph &G, int hu, int a0, int a1,
-                                                          int *moved_flag, Counters &K) {
+// residual as excess to v.  With PULL it is the h- form (Algorithm 7): every
+// residual arc v -> u with h(u) > h(v) + 1 is saturated, moving the residual
+// into u.  With a partition array pt only arcs within u's part count.
+// Returns this lane's share of the excess moved out of u (PULL: into u).
+template <bool PULL>
+__device__ __forceinline__ long long remove_invalid_range_t(const DevGraph &G, int hu, int a0, int a1,
+                                                            int *moved_flag, const unsigned char *pt,
+                                                            unsigned char side, Counters &K) {
     const int lane = threadIdx.x & 31;
     long long moved = 0;
     for (int b0 = a0; b0 < a1; b0 += 32 * kIlp) {
         ArcRound R;
-        load_round(G, b0, a1, R);
+        load_round_t<PULL>(G, b0, a1, R, pt, side);
         K.ri_arcs += round_arcs(b0, a1);
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             if (R.ra[j] > 0 && hu > R.hv[j] + 1) {
-                push_arc(G, b0 + 32 * j + lane, R.v[j], R.ra[j]);
+                move_arc<PULL>(G, b0 + 32 * j + lane, R.v[j], R.ra[j]);
                 moved += R.ra[j];
                 ++K.ri_moves;
                 *moved_flag = 1;
@@ -802,12 +887,19 @@ __device__ __forceinline__ long long remove_invalid_range(const DevGraph &G, int
     return moved;
 }
 
-__device__ __forceinline__ void remove_invalid_warp(const DevGraph &G, int u, int *moved_flag, Counters &K) {
+__device__ __forceinline__ long long remove_invalid_range(const DevGraph &G, int hu, int a0, int a1,
+                                                          int *moved_flag, Counters &K) {
+    return remove_invalid_range_t<false>(G, hu, a0, a1, moved_flag, nullptr, 0, K);
+}
+
+template <bool PULL>
+__device__ __forceinline__ void remove_invalid_warp_t(const DevGraph &G, int u, int *moved_flag,
+                                                      const unsigned char *pt, unsigned char side, Counters &K) {
     const int lane = threadIdx.x & 31;
     const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
     const int hu = __shfl_sync(kFull, lane == 0 ? lcg(&G.h[u]) : 0, 0);
-    const long long moved = warp_sum(remove_invalid_range(G, hu, beg, end, moved_flag, K));
-    if (lane == 0 && moved) add_ll(&G.e[u], -moved);
+    const long long moved = warp_sum(remove_invalid_range_t<PULL>(G, hu, beg, end, moved_flag, pt, side, K));
+    if (lane == 0 && moved) add_ll(&G.e[u], PULL ? moved : -moved);
 }
 
 // ------------------------------------------------------------ the kernel --
@@ -835,6 +927,9 @@ __device__ __forceinline__ void remove_invalid_warp(const DevGraph &G, int u, in
     } while (0)
 #define MF_SYNC(bucket) MF_SYNC_T(bucket, -1, 0, -1)
 
+// PP: the instance that can run Dynamic Push-Pull (Alg. 8); the plain
+// instance compiles without its code paths.
+template <bool PP>
 __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     Ctl *C = G.ctl;
     const int lane = threadIdx.x & 31;
@@ -868,6 +963,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         C->t_start = gtimer();
         if (TR) C->trace_n = 0;
     }
+
+    // Dynamic Push-Pull (Alg. 8) needs the exact cut of the previous state:
+    // T = {h < n} can reach a sink, S = {h >= n} cannot
+    const bool pp = PP && J.pp && kind == JOB_REPAIR && G.part && lcg(&C->cut_exact);
+    if (pp)
+        for (long long v = gtid; v < n; v += gthreads) G.part[v] = lcg(&G.h[v]) < n ? kPartT : kPartS;
 
     // ---- batch: validate, then apply (Algorithm 5) ----------------------
     bool fast = false;   // pure-increment batch that cannot change the cut
@@ -948,8 +1049,31 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 }
             }
             MF_SYNC(S_T_BATCH);
+            if (pp) {
+                // Alg. 8: saturate every residual arc from S to T.  Before the
+                // batch the cut had none, so only raised batch arcs can have one.
+                for (long long i = gtid; i < kb; i += gthreads) {
+                    if (lcg(&J.dlt[i]) <= 0) continue;
+                    const int a = __ldg(&G.arc_of_edge[J.ids[i]]);
+                    if (a < 0) continue;
+                    const int b = __ldg(&G.rev[a]);
+                    const int u = __ldg(&G.head[b]), v = __ldg(&G.head[a]);
+                    if (G.part[u] != kPartS || G.part[v] != kPartT) continue;
+                    const int ra = atomicExch(&G.r[a], 0);
+                    if (ra > 0) {
+                        atomicSub(&G.rr[b], ra);
+                        atomicAdd(&G.r[b], ra);
+                        atomicAdd(&G.rr[a], ra);
+                        add_ll(&G.e[u], -(long long)ra);
+                        add_ll(&G.e[v], (long long)ra);
+                    }
+                }
+                MF_SYNC(S_T_BATCH);
+            }
         }
     }
+    const bool pp_ran = pp && !fast;
+    int stage = pp_ran ? 1 : 0;   // 0 plain loop; push-pull: 1 push on T and pull on S, 2 push on P
 
     // ---- zero flow (Algorithm 1, first two loops) ------------------------
     if (kind == JOB_SOLVE || kind == JOB_RECOMPUTE) {
@@ -1018,9 +1142,23 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 bool root = false;
                 if (v < n) {
                     const long long ev = lcg(&G.e[v]);
-                    root = (v == t) || (v != s && ev < 0);
-                    G.h[v] = root ? 0 : n;
-                    if (root && v != t) dsum += ev;
+                    if (stage == 0) {
+                        root = (v == t) || (v != s && ev < 0);
+                        G.h[v] = root ? 0 : n;
+                        if (root && v != t) dsum += ev;
+                    } else if (stage == 1) {
+                        // Alg. 8: h+ roots are t and the deficient vertices of T,
+                        // h- roots are s and the overflowing vertices of S (both
+                        // heights live in h: the two sides are disjoint)
+                        root = G.part[v] == kPartT ? (v == t || ev < 0) : (v == s || ev > 0);
+                        G.h[v] = root ? 0 : n;
+                    } else {
+                        // the subgraph P: its deficient vertices are the sinks;
+                        // the rest of the graph sits at n + 1, out of reach
+                        const bool inP = G.part[v] == kPartP;
+                        root = inP && ev < 0;
+                        G.h[v] = inP ? (root ? 0 : n) : n + 1;
+                    }
                     if (root) rdeg += __ldg(&G.row[v + 1]) - __ldg(&G.row[v]);
                 }
                 warp_append(root, (int)v, &C->qcnt[0], G.qb0);
@@ -1062,18 +1200,21 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 C->asum[(L + 2) % 3] = 0;
                 if (bottom_up) ST[S_BU_LEVELS] += 1;
             }
+            const bool dual = PP && stage == 1;   // push-pull: backward on T, forward on S
             if (bottom_up) {
                 // groups of 32 consecutive vertex ids (warp w first, then tickets)
                 const int groups = (n + 31) / 32;
                 for (int grp = gwarp; grp < groups; grp = next_ticket(&C->gtk[L % 3], nwarps))
-                    bfs_bottom_up_group(G, grp * 32, L, ncnt, NF, asum, ccnt, K);
+                    bfs_bottom_up_group(G, grp * 32, dual, L, ncnt, NF, asum, ccnt, K);
             } else {
                 // groups of 32 frontier vertices (warp w first, then tickets)
                 for (int grp = gwarp; grp * 32 < cur; grp = next_ticket(&C->gtk[L % 3], nwarps)) {
                     const int idx = grp * 32 + lane;
                     int beg = 0, deg = 0;
+                    bool fwd = false;
                     if (idx < cur) {
                         const int u = lcg(&F[idx]);
+                        fwd = dual && G.part[u] == kPartS;
                         beg = __ldg(&G.row[u]);
                         deg = __ldg(&G.row[u + 1]) - beg;
                         if (deg > kBigDeg) {
@@ -1083,7 +1224,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             deg = 0;
                         }
                     }
-                    bfs_expand_warp(G, beg, deg, L, ncnt, NF, asum, K);
+                    bfs_expand_warp(G, beg, deg, fwd, dual, L, ncnt, NF, asum, K);
                 }
             }
             MF_SYNC_T(S_T_BFS, L, bottom_up ? 2 : 0, cur);
@@ -1092,9 +1233,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 for (int c = gwarp; c < nch; c = next_ticket(&C->ctk[L % 3], nwarps)) {
                     const int2 item = lcg(&G.cb[c]);
                     if (bottom_up) {
-                        bfs_bottom_up_item(G, item, L, ncnt, NF, asum, K);
+                        bfs_bottom_up_item(G, item, dual, L, ncnt, NF, asum, K);
                         continue;
                     }
+                    const unsigned fw = (dual && G.part[item.x] == kPartS) ? (1u << kIlp) - 1u : 0u;
                     const int a1 = min(item.y + kChunk, __ldg(&G.row[item.x + 1]));
                     for (int ab = item.y; ab < a1; ab += 32 * kIlp) {
                         int a[kIlp];
@@ -1104,7 +1246,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             a[j] = ab + 32 * j + lane;
                             ok[j] = a[j] < a1;
                         }
-                        bfs_visit_n(G, a, ok, L, ncnt, NF, asum, K);
+                        bfs_visit_n(G, a, ok, fw, dual, L, ncnt, NF, asum, K);
                     }
                 }
                 MF_SYNC_T(S_T_BFS, L, bottom_up ? 3 : 1, nch);
@@ -1116,7 +1258,19 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         // termination: no active vertex under the fresh BFS heights
         const int nw = lcg(&C->wcnt);
         const int nh = lcg(&C->hcnt);
-        if (nw == 0 && nh == 0) break;
+        if (nw == 0 && nh == 0) {
+            if (stage == 1) {
+                // Alg. 8: what neither search reached -- overflowing vertices
+                // of T that reach no sink, deficient vertices of S that no
+                // source reaches -- forms P, where the push phase continues
+                for (long long v = gtid; v < n; v += gthreads)
+                    if (v != s && v != t && lcg(&G.h[v]) == n) G.part[v] = kPartP;
+                MF_SYNC_T(S_T_RESET, 2, 0, 0);
+                stage = 2;
+                continue;
+            }
+            break;
+        }
         if (it >= J.max_iters) {
             if (gtid == 0) atomicOr(&C->status, ST_ITERS);
             break;
@@ -1169,7 +1323,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 C->hlc[0] = C->hlc[1] = 0;
                 ST[S_WL] += nhp;
             }
-            const ActList AL0{&C->wcnt, G.wl, wstamp, rstamp_it, pcnt, (pass & 1) ? G.hl : G.hl2, hstamp};
+            const ActList AL0{&C->wcnt, G.wl, wstamp, rstamp_it, pcnt, (pass & 1) ? G.hl : G.hl2, hstamp, stage == 1};
             bool pass_hubs_clean = true;
             if (nhp > 0) {
                 pass_hubs_clean = false;
@@ -1352,7 +1506,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 const int *list = G.wl;
                 for (int rd = 0;; ++rd) {
                     int *nlist = (rd & 1) ? G.qb0 : G.qb1;
-                    const ActList AL{&C->acnt[(rd + 1) % 3], nlist, snext++, rstamp_it, pcnt, AL0.hlist, hstamp};
+                    const ActList AL{&C->acnt[(rd + 1) % 3], nlist, snext++, rstamp_it, pcnt, AL0.hlist, hstamp,
+                                     stage == 1};
                     if (gtid == 0) {
                         C->acnt[(rd + 2) % 3] = 0;
                         C->rtk[(rd + 1) % 3] = 0;
@@ -1375,6 +1530,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                                 push_relabel_warp(G, base + j, kc, AL, K);
                             }
                         }
+                    } else if (stage == 1) {
+                        // push-pull: push on T (h+), pull on S (h-), each side
+                        // only over arcs within it
+                        for (int i = gwarp; i < cnt; i = next_ticket(&C->rtk[rd % 3], nwarps)) {
+                            const int u = lcg(&list[i]);
+                            const unsigned char side = G.part[u];
+                            if (side == kPartS)
+                                push_relabel_warp_t<true>(G, u, kc, AL, G.part, side, K);
+                            else
+                                push_relabel_warp_t<false>(G, u, kc, AL, G.part, side, K);
+                        }
                     } else {
                         for (int i = gwarp; i < cnt; i = next_ticket(&C->rtk[rd % 3], nwarps))
                             push_relabel_warp(G, lcg(&list[i]), kc, AL, K);
@@ -1396,15 +1562,26 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
 
         // RemoveInvalidEdges (Alg. 3): relabelled vertices by warps,
         // relabelled hubs by items
+        // (push-pull: only arcs within the vertex's part; the pull side uses
+        // the h- form, Algorithm 7)
+        const unsigned char *ptc = stage ? G.part : nullptr;
         const int nrl = lcg(&C->rlcnt);
-        for (int i = gwarp; i < nrl; i += nwarps) remove_invalid_warp(G, lcg(&G.rl[i]), &C->ri_moved[par], K);
+        for (int i = gwarp; i < nrl; i += nwarps) {
+            const int u = lcg(&G.rl[i]);
+            const unsigned char side = ptc ? ptc[u] : kPartT;
+            if (side == kPartS)
+                remove_invalid_warp_t<true>(G, u, &C->ri_moved[par], ptc, side, K);
+            else
+                remove_invalid_warp_t<false>(G, u, &C->ri_moved[par], ptc, side, K);
+        }
         const int nri = lcg(&C->rhcnt);
         for (int w = gwarp; w < nri; w += nwarps) {
             const int2 item = lcg(&G.hri[w]);
             const int u = item.x;
             const int hu = lcg(&G.h[u]);
             const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
-            const long long moved = warp_sum(remove_invalid_range(G, hu, item.y, a1, &C->ri_moved[par], K));
+            const long long moved = warp_sum(
+                remove_invalid_range_t<false>(G, hu, item.y, a1, &C->ri_moved[par], ptc, kPartP, K));
             if (lane == 0 && moved) add_ll(&G.e[u], -moved);
         }
         MF_SYNC_T(S_T_RI, 0, 0, nrl + nri);
@@ -1420,7 +1597,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         const int busy = (rounds_clean ? 0 : 1) | (hubs_clean ? 0 : 2) | (lcg(&C->ri_moved[par]) ? 4 : 0) |
                          (pend > 0 ? 8 : 0);
         if (gtid == 0 && TR && C->trace_n - 1 < G.trace_cap) TR[C->trace_n - 1].mode = (short)busy;
-        if (!J.exact_exit && kind != JOB_REFRESH && busy == 0) {
+        if (!J.exact_exit && kind != JOB_REFRESH && stage == 0 && busy == 0) {
             long long dsum = 0;
             for (long long v = gtid; v < n; v += gthreads) {
                 const long long ev = lcg(&G.e[v]);
@@ -1434,15 +1611,35 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         }
     }
 
+    if (pp_ran) {
+        // Alg. 8's result: the new cut is S' = (S minus P) plus the part of P
+        // that reaches no sink of P, T' the rest; every deficient vertex ended
+        // in T', so the value is e(t) plus all deficits (recounted here).
+        // The heights are rewritten to encode the cut for the next repair
+        // (T' below n, S' at n): exact as a cut, not as BFS distances.
+        long long dsum = 0;
+        for (long long v = gtid; v < n; v += gthreads) {
+            const long long ev = lcg(&G.e[v]);
+            if (v != s && v != t && ev < 0) dsum += ev;
+            const unsigned char p = G.part[v];
+            if (p == kPartT) G.h[v] = 0;
+            else if (p == kPartS) G.h[v] = n;
+        }
+        dsum = warp_sum(dsum);
+        if (lane == 0 && dsum) add_ll(&C->dacc[(it & 1) ^ 1], dsum);
+        MF_SYNC_T(S_T_RESET, 3, 0, 0);
+    }
+
     // ---- result and statistics -------------------------------------------
     if (gtid == 0) {
-        // dacc: deficits at the last height init, or recounted at a clean exit
-        if (!fast) C->flow = lcg(&G.e[t]) + lcg(&C->dacc[early ? (it & 1) ^ 1 : it & 1]);
+        // dacc: deficits at the last height init, or recounted at a clean
+        // exit and after a push-pull repair
+        if (!fast) C->flow = lcg(&G.e[t]) + lcg(&C->dacc[(early || pp_ran) ? (it & 1) ^ 1 : it & 1]);
         if (kind != JOB_REFRESH) {
             C->iters = fast ? 0 : early ? it + 1 : it;
-            C->exit_kind = fast ? EXIT_NO_CUT_CHANGE : early ? EXIT_CLEAN : EXIT_BFS;
+            C->exit_kind = fast ? EXIT_NO_CUT_CHANGE : early ? EXIT_CLEAN : pp_ran ? EXIT_PUSH_PULL : EXIT_BFS;
         }
-        C->heights_exact = !fast && !early;
+        C->heights_exact = !fast && !early && !pp_ran;
         C->cut_exact = !early;   // the fast path keeps the exact cut it started from
         C->ri_moved[0] = C->ri_moved[1] = 0;
         C->phc[0] = C->phc[1] = 0;
@@ -1754,7 +1951,10 @@ int launch(mf_graph *g, const Job &job, cudaStream_t st) {
     jb.st = job.kind == JOB_REFRESH ? g->dg.ctl->st_aux : g->dg.ctl->st;
     jb.trace = job.kind == JOB_REFRESH ? nullptr : g->dg.trace;
     void *args[] = {&dg, &jb};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_solve, dim3(g->grid), dim3(kBlock), args, 0, st);
+    // a push-pull graph keeps its cut exact: every job ends on a BFS
+    if (g->opt.mode == MF_MODE_PUSH_PULL) jb.exact_exit = 1;
+    const void *fn = job.pp ? (const void *)k_solve<true> : (const void *)k_solve<false>;
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(g->grid), dim3(kBlock), args, 0, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_err(MF_ECUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
@@ -1905,14 +2105,20 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
         return set_err(code, msg);
     };
     if ((g->opt.alloc == nullptr) != (g->opt.free == nullptr)) return fail(MF_EINVAL, "alloc and free must both be set");
-    if (g->opt.mode != MF_MODE_DATA_DRIVEN && g->opt.mode != MF_MODE_TOPOLOGY) return fail(MF_EINVAL, "unknown mode");
+    if (g->opt.mode != MF_MODE_DATA_DRIVEN && g->opt.mode != MF_MODE_TOPOLOGY && g->opt.mode != MF_MODE_PUSH_PULL)
+        return fail(MF_EINVAL, "unknown mode");
     if (cudaGetDevice(&g->dev) != cudaSuccess) return fail(MF_ECUDA, "no CUDA device");
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->dev);
     cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->dev);
     if (!coop) return fail(MF_ECUDA, "device does not support cooperative launch");
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, kBlock, 0) != cudaSuccess || per_sm < 1)
+    int per_sm_pp = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<false>, kBlock, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_pp, k_solve<true>, kBlock, 0) != cudaSuccess)
+        return fail(MF_ECUDA, "occupancy query failed");
+    per_sm = std::min(per_sm, per_sm_pp);
+    if (per_sm < 1)
         return fail(MF_ECUDA, "occupancy query failed");
     g->grid = per_sm * g->sms;
     if (g->opt.grid_blocks > 0) g->grid = std::min(g->grid, int(g->opt.grid_blocks));
@@ -1951,6 +2157,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     D.astamp = dnew<unsigned>(g, N);
     D.rstamp = dnew<unsigned>(g, N);
     D.rl = dnew<int>(g, N);
+    D.part = g->opt.mode == MF_MODE_PUSH_PULL ? dnew<unsigned char>(g, N) : nullptr;
     D.ctl = dnew<Ctl>(g, 1);
     g->side_buf = dnew<unsigned char>(g, N);
     if (!row || !head || !rev || !aoe || !D.cap || !D.r || !D.rr || !D.h || !D.e || !D.cap_edge || !D.stamp ||
@@ -2039,6 +2246,7 @@ int mf_apply_updates(mf_graph *g, int64_t k, const int32_t *edge_id, const int32
     j.flags = flags;
     j.kc = g->kc;
     j.mode = g->opt.mode;
+    j.pp = g->opt.mode == MF_MODE_PUSH_PULL;
     j.max_iters = g->max_iters;
     j.time_limit_ns = g->time_limit_ns;
     j.ids = ids;
@@ -2086,6 +2294,7 @@ int mf_apply_updates_dev(mf_graph *g, const int32_t *k_dev, int64_t k_max, const
     j.flags = flags;
     j.kc = g->kc;
     j.mode = g->opt.mode;
+    j.pp = g->opt.mode == MF_MODE_PUSH_PULL;
     j.max_iters = g->max_iters;
     j.time_limit_ns = g->time_limit_ns;
     j.ids = edge_id;
@@ -2383,7 +2592,7 @@ int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const in
         int per_sm = 0, sms = 0;
         if (D.err == cudaSuccess) D.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (D.err == cudaSuccess)
-            D.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, kBlock, 0);
+            D.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<false>, kBlock, 0);
         D.grid = std::min(per_sm * sms, kNoAllocMaxGrid);
         if (D.err == cudaSuccess && D.grid < 1) D.err = cudaErrorInvalidConfiguration;
     });
@@ -2433,7 +2642,7 @@ int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const in
     j.max_iters = 4LL * n + 1000;
     j.time_limit_ns = 60ull * 1000ull * 1000ull * 1000ull;
     void *args[] = {&D, &j};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_solve, dim3(ND.grid), dim3(kBlock), args, 0, st);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_solve<false>, dim3(ND.grid), dim3(kBlock), args, 0, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_err(MF_ECUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));

@@ -209,13 +209,14 @@ def _specs():
         return make
 
     out = []
-    for s in range(20):
-        out.append((f"random_s{s}", len(out), lambda s=s: gen.random_graph(seed=s), mixed(1, 50, 5, 0.5), 100))
-    for sc, seeds, nb in ((14, 8, 100), (16, 4, 80), (18, 2, 40), (20, 1, 30)):
+    for s in range(60):
+        out.append((f"random_s{s}", len(out), lambda s=s: gen.random_graph(seed=s), mixed(1, 50, 5, 0.5), 150))
+    for sc, seeds, nb in ((14, 24, 200), (16, 12, 150), (18, 6, 100), (20, 4, 60)):
         for s in range(seeds):
             out.append((f"rmat{sc}_s{s}", len(out), lambda sc=sc, s=s: gen.rmat(scale=sc, seed=100 + s),
                         mixed(1, 500, 100, 0.08), nb))
-    for W, seeds, nb, lo, hi in ((512, 2, 40, 16, 128), (1024, 1, 30, 64, 512)):
+    for W, seeds, nb, lo, hi in ((512, 8, 80, 16, 128), (1024, 4, 50, 32, 256), (2048, 2, 30, 64, 512),
+                                 (4096, 1, 15, 64, 512)):
         for s in range(seeds):
             out.append((f"grid{W}_s{s}", len(out), lambda W=W, s=s: gen.grid_segmentation(W, W, seed=200 + s),
                         rect(lo, hi), nb))

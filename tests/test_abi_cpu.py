@@ -115,3 +115,16 @@ def test_product_path_has_no_fallback(mf, tmp_path, monkeypatch):
     monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         _native.lib()
+
+
+def test_header_constants_match_binding(mf):
+    """Every MF_* constant the binding defines has the value include/mf.h gives it."""
+    from paper_2511_05895_gb300 import _native
+    text = open(os.path.join(ROOT, "include", "mf.h")).read()
+    defs = dict(re.findall(r"#define\s+(MF_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+|\d+)", text))
+    checked = 0
+    for name, val in defs.items():
+        if hasattr(_native, name):
+            assert getattr(_native, name) == int(val, 0), name
+            checked += 1
+    assert checked >= 15, checked

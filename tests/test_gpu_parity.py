@@ -434,3 +434,36 @@ def test_pure_increment_fast_path(mf):
     assert G.stats()["exit_kind"] != 2
     certify_gpu(G, g, cap, G.flow_value())
     G.close()
+
+
+@pytest.mark.parametrize("case", ["config1", "rmat12", "rmat15", "grid"])
+def test_push_pull_mode(mf, case):
+    """MF_MODE_PUSH_PULL (Dynamic Push-Pull, Alg. 8): every repair is a
+    push-pull repair (exit_kind 3), every value equals the oracle's and every
+    state passes the certificate."""
+    if case == "config1":
+        g = gen.random_graph(seed=81)
+        mk = lambda cap, i: gen.mixed_batch(cap, 50, 1, 50, seed=81, index=i)  # noqa: E731
+    elif case.startswith("rmat"):
+        g = gen.rmat(scale=int(case[4:]), seed=82)
+        mk = lambda cap, i: gen.mixed_batch(cap, max(10, g.m // (100 if i % 2 else 1000)), 1, 500,  # noqa: E731
+                                            seed=82, index=i)
+    else:
+        g = gen.grid_segmentation(192, 128, seed=83)
+        mk = lambda cap, i: gen.grid_rect_batch(g, seed=83, index=i, side_lo=8, side_hi=64)  # noqa: E731
+    cap = g.cap.copy()
+    G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t, mode=mf.MF_MODE_PUSH_PULL)
+    G.solve()
+    assert G.flow_value() == oracle_flow(g, cap)
+    kinds = []
+    for i in range(4):
+        b = mk(cap, i)
+        G.apply_updates(b.edge_id, b.new_cap)
+        gen.apply_batch(cap, b)
+        f = G.flow_value()
+        kinds.append(G.stats()["exit_kind"])
+        assert f == oracle_flow(g, cap), (case, i)
+        if i % 2:
+            certify_gpu(G, g, cap, f)
+    assert set(kinds) <= {2, 3} and 3 in kinds, kinds
+    G.close()
