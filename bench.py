@@ -281,13 +281,16 @@ def grid_measurement(batches: int, flush, peak: float, seed: int = 3) -> dict:
     measured HBM bandwidth, and a check that both give the same value."""
     import torch
     from paper_2511_05895_gb300 import MaxFlowGraph
+    from paper_2511_05895_gb300 import MF_MODE_PUSH_PULL
     g = gen.grid_segmentation(4096, 4096, seed=seed)
     G = MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=4)
     G.solve()
     G.flow_value()
+    Gp = MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=4, mode=MF_MODE_PUSH_PULL)
+    Gp.solve()
     stream = torch.cuda.current_stream()
     empty = torch.zeros(0, dtype=torch.int32, device="cuda")
-    dyn, sta, ks, fr = [], [], [], []
+    dyn, sta, ks, fr, ppt = [], [], [], [], []
     equal = True
     for i in range(batches):
         b = gen.grid_rect_batch(g, seed=seed, index=i)
@@ -307,25 +310,52 @@ def grid_measurement(batches: int, flush, peak: float, seed: int = 3) -> dict:
         ev[3].record(stream)
         ev[3].synchronize()
         equal = equal and G.flow_value() == f_dyn
+        ppt.append(time_repairs(Gp, [(ids, cp)], 0, flush, stream)[0][0])
+        equal = equal and Gp.flow_value() == f_dyn
         d, s_ = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
         dyn.append(d)
         sta.append(s_)
         ks.append(len(b.edge_id))
         fr.append(algorithmic_bytes(st, g.n) / (d * 1e-3) / 1e9 / peak)
     G.close()
-    d, s_ = statistics.median(dyn), statistics.median(sta)
+    Gp.close()
+    d, s_, pm = statistics.median(dyn), statistics.median(sta), statistics.median(ppt)
     return {"workload": f"segmentation grid 4096^2 (n={g.n}, m={g.m}), rectangle batches of side 64-512 "
                         "rewriting terminal capacities", "batches": batches,
             "entries_median": int(statistics.median(ks)), "dynamic_ms": round(d, 3),
-            "static_recompute_ms": round(s_, 3), "speedup": round(s_ / d, 3),
+            "push_pull_ms": round(pm, 3), "static_recompute_ms": round(s_, 3), "speedup": round(s_ / d, 3),
+            "push_pull_speedup": round(s_ / pm, 3),
             "hbm_frac_of_measured": round(statistics.median(fr), 4), "values_equal": equal}
+
+
+MODES = {"data-driven": 0, "topology": 1, "push-pull": 2}
+
+
+def time_repairs(G, dev, warmup, flush, stream):
+    """Apply dev[:warmup] untimed, then time each remaining batch on the
+    device (L2 flushed before each); returns (ms list, stats list)."""
+    import torch
+    for ids, caps in dev[:warmup]:
+        G.apply_updates(ids, caps)
+    G.sync()
+    ms, sts = [], []
+    for ids, caps in dev[warmup:]:
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        G.apply_updates(ids, caps)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        sts.append(G.stats())
+    return ms, sts
 
 
 def workload_config(args, g) -> dict:
     return {"workload": f"RMAT scale {SCALE} (n={g.n}, m={g.m}, a=0.57 b=0.19 c=0.19), caps U[1,1000], "
                         f"mixed batches of {args.batch} edges (+/-U[1,500])",
             "n": g.n, "m": g.m, "batch_edges": args.batch, "seed": SEED,
-            "kernel_cycles": args.kc, "policy": args.policy,
+            "kernel_cycles": args.kc, "policy": args.policy, "mode": args.mode,
             "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -343,6 +373,9 @@ def main():
     ap.add_argument("--no-grid", action="store_true", help="skip the 4096^2 segmentation-grid measurement")
     ap.add_argument("--policy", default="fixed", choices=["fixed", "plain", "learned"],
                     help="batch policy: fixed repair, the plain rule, or the trained network")
+    ap.add_argument("--mode", default="data-driven", choices=list(MODES),
+                    help="processing mode of the timed repairs (Sec. 5.2 / 5.3 / Alg. 8)")
+    ap.add_argument("--no-pp", action="store_true", help="skip the Dynamic Push-Pull comparison")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -367,7 +400,7 @@ def main():
 
     g = gen.rmat(scale=SCALE, seed=SEED + 1000 * rank)
     cap = g.cap.copy()
-    G = MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t, kernel_cycles=args.kc)
+    G = MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t, kernel_cycles=args.kc, mode=MODES[args.mode])
     G.solve()
     flow0 = G.flow_value()
     if args.policy != "fixed":
@@ -433,6 +466,22 @@ def main():
     except AssertionError:
         certified = False
 
+    # ---- the same batches repaired by Dynamic Push-Pull (Alg. 8) ----------
+    pp, Gp = None, None
+    if not args.no_pp and args.mode != "push-pull" and args.policy == "fixed":
+        from paper_2511_05895_gb300 import MF_MODE_PUSH_PULL
+        Gp = MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=args.kc, mode=MF_MODE_PUSH_PULL)
+        Gp.solve()
+        pms, psts = time_repairs(Gp, dev, args.warmup, flush, stream)
+        p_ms = sum(pms) / len(pms)
+        p_bytes = sum(algorithmic_bytes(st, g.n) for st in psts) / len(psts)
+        pp = {"mode": "push-pull (MF_MODE_PUSH_PULL, Alg. 8)", "ms_per_step": round(p_ms, 4),
+              "value": round(1000.0 / p_ms, 2), "unit": UNIT,
+              "speedup_vs_headline_mode": round((1000.0 * t_total / args.steps) / p_ms, 3),
+              "hbm_frac_of_measured": None, "algorithmic_bytes_per_launch": int(p_bytes),
+              "exit_kinds": sorted({st["exit_kind"] for st in psts}),
+              "value_equal": Gp.flow_value() == flow_after}
+
     # ---- e2e through the C ABI with pinned host buffers ------------------
     e2e_batches = make_batches(host_cap, args.batch, args.steps, 5_000)
     pinned = [(torch.from_numpy(b.edge_id).pin_memory(), torch.from_numpy(b.new_cap).pin_memory()) for b in e2e_batches]
@@ -446,6 +495,9 @@ def main():
         G.flow_value()
         t_e2e += time.perf_counter() - t0
     e2e_value = replicas.whole_job_rate(args.steps, t_e2e, device="cuda")
+    if Gp is not None:   # keep the push-pull instance on the same capacities
+        for ids, caps in pinned:
+            Gp.apply_updates(ids, caps)
 
     # ---- dynamic vs static recompute per batch size ----------------------
     sizes = {}
@@ -453,13 +505,15 @@ def main():
         empty = (torch.zeros(0, dtype=torch.int32, device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"))
         for j, k in enumerate((1_000, 10_000, 100_000, 1_000_000)):
             bs = make_batches(host_cap, k, 3, 20_000 + 10 * j)
-            dyn, sta = [], []
+            dyn, sta, ppt = [], [], []
             for b in bs:
                 ids = torch.from_numpy(b.edge_id).cuda()
                 cp = torch.from_numpy(b.new_cap).cuda()
                 a0, a1 = timed_step(ids, cp)
                 a1.synchronize()
                 dyn.append(a0.elapsed_time(a1))
+                if Gp is not None:
+                    ppt.append(time_repairs(Gp, [(ids, cp)], 0, flush, stream)[0][0])
                 s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 flush.zero_()
                 s0.record(stream)
@@ -471,6 +525,11 @@ def main():
             d, s = statistics.median(dyn), statistics.median(sta)
             sizes[str(k)] = {"dynamic_ms": round(d, 4), "static_recompute_ms": round(s, 4),
                              "speedup": round(s / d, 3), "frac_of_edges": round(k / g.m, 6)}
+            if ppt:
+                pm = statistics.median(ppt)
+                sizes[str(k)].update(push_pull_ms=round(pm, 4), push_pull_speedup=round(s / pm, 3))
+    if Gp is not None:
+        Gp.close()
 
     # ---- CPU oracle on a bounded sample ----------------------------------
     cpu = None
@@ -492,6 +551,9 @@ def main():
         peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
+
+    if pp is not None:
+        pp["hbm_frac_of_measured"] = round(pp["algorithmic_bytes_per_launch"] / (pp["ms_per_step"] * 1e-3) / 1e9 / peak, 4)
 
     grid = None
     if not args.no_grid and rank == 0:
@@ -531,6 +593,7 @@ def main():
         "clocks": clk,
         "cpu_baseline": cpu,
         "checks": {"flow_initial": flow0, "flow_final": flow_after, "certified": certified},
+        "push_pull": pp,
         "grid": grid,
         "serving": serving,
     }
