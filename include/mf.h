@@ -71,10 +71,13 @@ extern "C" {
                                   push on its sink side and pull on its source
                                   side concurrently, then push on the leftover
                                   subgraph P.  Needs the exact cut of the
-                                  previous state (after mf_solve, a BFS-ended or
-                                  push-pull repair); otherwise that repair runs
-                                  the plain dynamic loop.  exit_kind 3 marks a
-                                  push-pull repair.                            */
+                                  previous state, which every job of such a
+                                  graph keeps by ending on a BFS.  exit_kind 3
+                                  marks a push-pull repair.  Solves from zero
+                                  flow (mf_solve, MF_RECOMPUTE) use static
+                                  push-pull (Sec. 4.2): the arcs into t are
+                                  saturated too and the vertices left deficient
+                                  are sinks of the loop.                       */
 
 typedef struct mf_graph mf_graph;
 

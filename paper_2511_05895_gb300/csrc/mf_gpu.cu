@@ -169,6 +169,7 @@ struct Job {
     int kind, k, flags, kc, mode;
     int exact_exit;      // 1: stop only after a BFS finds no active vertex
     int pp;              // 1: a repair by Dynamic Push-Pull (Alg. 8) when the cut is exact
+    int sink_sat;        // 1: a solve from zero flow also saturates the arcs into t
     long long *st;       // statistics array (Ctl::st, or Ctl::st_aux for JOB_REFRESH)
     TraceRec *trace;     // trace records, or nullptr
     const int *k_dev;    // if set, the batch size is read from device memory
@@ -346,7 +347,7 @@ __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (
         K.bfs_verts += disc[j];
         // a vertex of the pull side (forward search) is active when deficient
         const bool act = disc[j] && (((fwd >> j) & 1u) ? ev[j] < 0 : ev[j] > 0);
-        hub[j] = act && !dual && deg[j] > kHubDeg;
+        hub[j] = act && deg[j] > kHubDeg;
         small[j] = act && !hub[j];
     }
     ds = warp_sum(ds);
@@ -374,7 +375,7 @@ __device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int
     const long long ds = warp_sum((long long)deg);
     if ((threadIdx.x & 31) == 0 && ds) add_ll(asum, ds);
     if (__ballot_sync(kFull, act)) {
-        const bool hub = act && !dual && deg > kHubDeg;
+        const bool hub = act && deg > kHubDeg;
         warp_append(act && !hub, v, &G.ctl->wcnt, G.wl);
         warp_append(hub, v, &G.ctl->hcnt, G.hl);
     }
@@ -586,7 +587,6 @@ struct ActList {
     int *hcnt;         // the next pass's hub list (high-degree vertices a push
     int *hlist;        //   turned active), its size and its stamp
     unsigned hstamp;
-    bool dual;         // first stage of a push-pull repair: no hub lists
 };
 
 // A vertex whose height PushRelabel raised joins the relabel list of the loop
@@ -599,9 +599,8 @@ __device__ __forceinline__ void note_relabel(const DevGraph &G, int u, unsigned 
 
 // A push of d units raised e(v) from `old` (a pull lowered it): if v turned
 // active (excess positive -- for a pull, negative -- below height n, not s or
-// t) it joins the next activation round when its degree is <= kHubDeg or in
-// the first stage of a push-pull repair, else the hub list of the next
-// PushRelabel pass.  All 32 lanes call.
+// t) it joins the next activation round when its degree is <= kHubDeg, else
+// the hub list of the next PushRelabel pass.  All 32 lanes call.
 template <bool PULL>
 __device__ __forceinline__ void note_activation_t(const DevGraph &G, bool moved, int v, long long old, long long d,
                                                   const ActList &AL) {
@@ -609,7 +608,7 @@ __device__ __forceinline__ void note_activation_t(const DevGraph &G, bool moved,
     const bool turned = PULL ? (old >= 0 && old - d < 0) : (old <= 0 && old + d > 0);
     if (moved && turned && v != G.s && v != G.t) {
         if (lcg(&G.h[v]) < G.n) {
-            if (AL.dual || __ldg(&G.row[v + 1]) - __ldg(&G.row[v]) <= kHubDeg)
+            if (__ldg(&G.row[v + 1]) - __ldg(&G.row[v]) <= kHubDeg)
                 add = atomicExch(&G.astamp[v], AL.stamp) != AL.stamp;
             else
                 add_hub = atomicExch(&G.astamp[v], AL.hstamp) != AL.hstamp;
@@ -902,6 +901,67 @@ __device__ __forceinline__ void remove_invalid_warp_t(const DevGraph &G, int u, 
     if (lane == 0 && moved) add_ll(&G.e[u], PULL ? moved : -moved);
 }
 
+// Hub cycle helpers (the cooperative PushRelabel of high-degree vertices).
+// H1 scan of one kPrChunk-arc item [a0, a1) of hub u (first arc beg): the
+// lowest (height, arc) key over its residual arcs (PULL: arcs into u).
+template <bool PULL>
+__device__ __forceinline__ unsigned long long hub_scan_item(const DevGraph &G, int a0, int a1, int beg,
+                                                            const unsigned char *pt, unsigned char side,
+                                                            Counters &K) {
+    unsigned long long best = ~0ull;
+    for (; a0 < a1; a0 += 32 * kIlp) {
+        ArcRound R;
+        load_round_t<PULL>(G, a0, a1, R, pt, side);
+        K.pr_arcs += round_arcs(a0, a1);
+        const unsigned long long k = round_min_key(R, a0, beg);
+        best = k < best ? k : best;
+    }
+    return best;
+}
+
+// H3 of one item: moves along the item's residual arcs at height hh, in arc
+// order, each warp reserving its share of what the hub has left to move
+// (*rem) with one atomic.  Returns the amount this warp moved (all lanes).
+template <bool PULL>
+__device__ __forceinline__ long long hub_move_item(const DevGraph &G, int a0, int a1, int hh, long long *rem,
+                                                   const ActList &AL, const unsigned char *pt, unsigned char side,
+                                                   Counters &K) {
+    const int lane = threadIdx.x & 31;
+    long long sent = 0;
+    for (; a0 < a1; a0 += 32 * kIlp) {
+        ArcRound R;
+        load_round_t<PULL>(G, a0, a1, R, pt, side);
+        K.pr_arcs += round_arcs(a0, a1);
+        int ra[kIlp];
+        long long incl[kIlp], tot = 0;
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            ra[j] = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
+            incl[j] = warp_incl_scan(ra[j]) + tot;   // arc order: round j, then lane
+            tot = __shfl_sync(kFull, incl[j], 31);
+        }
+        if (tot == 0) continue;
+        long long old = 0;
+        if (lane == 0)
+            old = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(rem), (unsigned long long)(-tot));
+        old = __shfl_sync(kFull, old, 0);
+        if (old <= 0) break;
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            long long d = old - (incl[j] - ra[j]);
+            d = d < 0 ? 0 : (d > ra[j] ? ra[j] : d);
+            long long prev = 0;
+            if (d > 0) {
+                prev = move_arc<PULL>(G, a0 + 32 * j + lane, R.v[j], (int)d);
+                sent += d;
+                ++K.push;
+            }
+            note_activation_t<PULL>(G, d > 0, R.v[j], prev, d, AL);
+        }
+    }
+    return warp_sum(sent);
+}
+
 // ------------------------------------------------------------ the kernel --
 // Grid barrier inside k_solve; CTA 0's thread 0 charges the time since the
 // previous barrier to a phase bucket of the statistics and, when tracing is
@@ -1106,6 +1166,28 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         }
         moved = warp_sum(moved);
         if (lane == 0 && moved) add_ll(&G.e[s], -moved);
+        MF_SYNC(S_T_BATCH);
+    }
+
+    // ---- static push-pull (Sec. 4.2): also saturate every arc into t; the
+    // vertices left deficient become secondary sinks of the loop below
+    if (J.sink_sat && (kind == JOB_SOLVE || kind == JOB_RECOMPUTE)) {
+        long long moved = 0;
+        const int a0 = __ldg(&G.row[t]), a1 = __ldg(&G.row[t + 1]);
+        for (long long a = a0 + gtid; a < a1; a += gthreads) {
+            const int rin = lcg(&G.rr[a]);   // residual of v -> t
+            if (rin > 0) {
+                const int b = __ldg(&G.rev[a]);
+                G.r[b] = 0;
+                G.rr[a] = 0;
+                atomicAdd(&G.r[a], rin);
+                atomicAdd(&G.rr[b], rin);
+                add_ll(&G.e[__ldg(&G.head[a])], -(long long)rin);
+                moved += rin;
+            }
+        }
+        moved = warp_sum(moved);
+        if (lane == 0 && moved) add_ll(&G.e[t], moved);
         MF_SYNC(S_T_BATCH);
     }
 
@@ -1323,7 +1405,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 C->hlc[0] = C->hlc[1] = 0;
                 ST[S_WL] += nhp;
             }
-            const ActList AL0{&C->wcnt, G.wl, wstamp, rstamp_it, pcnt, (pass & 1) ? G.hl : G.hl2, hstamp, stage == 1};
+            const ActList AL0{&C->wcnt, G.wl, wstamp, rstamp_it, pcnt, (pass & 1) ? G.hl : G.hl2, hstamp};
             bool pass_hubs_clean = true;
             if (nhp > 0) {
                 pass_hubs_clean = false;
@@ -1364,15 +1446,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         // no push or relabel runs during H1, so every item of a hub
                         // sees the same e(u), h(u): the items of a hub that is no
                         // longer active skip the scan and only arrive
-                        const bool live = lcg(&G.e[u]) > 0 && lcg(&G.h[u]) < n;
+                        // (a hub of the pull side of a push-pull repair is
+                        // active when deficient and scans its arcs in)
+                        const unsigned char side = stage == 1 ? G.part[u] : kPartT;
+                        const bool pull = PP && side == kPartS;
+                        const long long eu0 = lcg(&G.e[u]);
+                        const bool live = (pull ? eu0 < 0 : eu0 > 0) && lcg(&G.h[u]) < n;
+                        const unsigned char *ptc = stage == 1 ? G.part : nullptr;
                         unsigned long long best = ~0ull;
-                        for (int a0 = item.y; live && a0 < a1; a0 += 32 * kIlp) {
-                            ArcRound R;
-                            load_round(G, a0, a1, R);
-                            K.pr_arcs += round_arcs(a0, a1);
-                            const unsigned long long k = round_min_key(R, a0, beg);
-                            best = k < best ? k : best;
-                        }
+                        if (live)
+                            best = pull ? hub_scan_item<true>(G, item.y, a1, beg, ptc, side, K)
+                                        : hub_scan_item<false>(G, item.y, a1, beg, ptc, side, K);
                         best = warp_min(best);
                         int decided = -2;   // -2: not the deciding warp; else the hub's mode
                         bool relabelled = false;
@@ -1383,7 +1467,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             if (atomicAdd(&G.hdone[i], 1) == lcg(&G.hnit[i]) - 1) {
                                 __threadfence();
                                 const int hu = lcg(&G.h[u]);
-                                const long long eu = lcg(&G.e[u]);
+                                const long long eu = pull ? -lcg(&G.e[u]) : lcg(&G.e[u]);   // amount to move
                                 const unsigned long long key = __ldcg(&G.hkey[i]);
                                 G.hkey[i] = ~0ull;
                                 G.hdone[i] = 0;
@@ -1456,41 +1540,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         const int hh = mode - 1;
                         const int u = lcg(&HL[item.x]);
                         const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
-                        long long sent = 0;
-                        for (int a0 = item.y; a0 < a1; a0 += 32 * kIlp) {
-                            ArcRound R;
-                            load_round(G, a0, a1, R);
-                            K.pr_arcs += round_arcs(a0, a1);
-                            int ra[kIlp];
-                            long long incl[kIlp], tot = 0;
-#pragma unroll
-                            for (int j = 0; j < kIlp; ++j) {
-                                ra[j] = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
-                                incl[j] = warp_incl_scan(ra[j]) + tot;   // arc order: round j, then lane
-                                tot = __shfl_sync(kFull, incl[j], 31);
-                            }
-                            if (tot == 0) continue;
-                            long long old = 0;
-                            if (lane == 0)
-                                old = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&G.hrem[item.x]),
-                                                           (unsigned long long)(-tot));
-                            old = __shfl_sync(kFull, old, 0);
-                            if (old <= 0) break;
-#pragma unroll
-                            for (int j = 0; j < kIlp; ++j) {
-                                long long d = old - (incl[j] - ra[j]);
-                                d = d < 0 ? 0 : (d > ra[j] ? ra[j] : d);
-                                long long prev = 0;
-                                if (d > 0) {
-                                    prev = push_arc(G, a0 + 32 * j + lane, R.v[j], (int)d);
-                                    sent += d;
-                                    ++K.push;
-                                }
-                                note_activation(G, d > 0, R.v[j], prev, d, AL0);
-                            }
+                        const unsigned char side = stage == 1 ? G.part[u] : kPartT;
+                        const unsigned char *ptc = stage == 1 ? G.part : nullptr;
+                        if (PP && side == kPartS) {
+                            const long long got = hub_move_item<true>(G, item.y, a1, hh, &G.hrem[item.x], AL0, ptc,
+                                                                      side, K);
+                            if (lane == 0 && got) add_ll(&G.e[u], got);
+                        } else {
+                            const long long sent = hub_move_item<false>(G, item.y, a1, hh, &G.hrem[item.x], AL0,
+                                                                        ptc, side, K);
+                            if (lane == 0 && sent) add_ll(&G.e[u], -sent);
                         }
-                        sent = warp_sum(sent);
-                        if (lane == 0 && sent) add_ll(&G.e[u], -sent);
                     }
                     MF_SYNC_T(S_T_HUB, c, 3, lcg(&C->hub_act[c & 1]));
                     if (lcg(&C->hub_act[c & 1]) == 0) {
@@ -1506,8 +1566,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 const int *list = G.wl;
                 for (int rd = 0;; ++rd) {
                     int *nlist = (rd & 1) ? G.qb0 : G.qb1;
-                    const ActList AL{&C->acnt[(rd + 1) % 3], nlist, snext++, rstamp_it, pcnt, AL0.hlist, hstamp,
-                                     stage == 1};
+                    const ActList AL{&C->acnt[(rd + 1) % 3], nlist, snext++, rstamp_it, pcnt, AL0.hlist, hstamp};
                     if (gtid == 0) {
                         C->acnt[(rd + 2) % 3] = 0;
                         C->rtk[(rd + 1) % 3] = 0;
@@ -1580,9 +1639,16 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             const int u = item.x;
             const int hu = lcg(&G.h[u]);
             const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
-            const long long moved = warp_sum(
-                remove_invalid_range_t<false>(G, hu, item.y, a1, &C->ri_moved[par], ptc, kPartP, K));
-            if (lane == 0 && moved) add_ll(&G.e[u], -moved);
+            const unsigned char side = stage == 1 ? G.part[u] : (stage == 2 ? kPartP : kPartT);
+            if (PP && side == kPartS) {
+                const long long got = warp_sum(
+                    remove_invalid_range_t<true>(G, hu, item.y, a1, &C->ri_moved[par], ptc, side, K));
+                if (lane == 0 && got) add_ll(&G.e[u], got);
+            } else {
+                const long long moved = warp_sum(
+                    remove_invalid_range_t<false>(G, hu, item.y, a1, &C->ri_moved[par], ptc, side, K));
+                if (lane == 0 && moved) add_ll(&G.e[u], -moved);
+            }
         }
         MF_SYNC_T(S_T_RI, 0, 0, nrl + nri);
 
@@ -1951,8 +2017,12 @@ int launch(mf_graph *g, const Job &job, cudaStream_t st) {
     jb.st = job.kind == JOB_REFRESH ? g->dg.ctl->st_aux : g->dg.ctl->st;
     jb.trace = job.kind == JOB_REFRESH ? nullptr : g->dg.trace;
     void *args[] = {&dg, &jb};
-    // a push-pull graph keeps its cut exact: every job ends on a BFS
-    if (g->opt.mode == MF_MODE_PUSH_PULL) jb.exact_exit = 1;
+    // a push-pull graph keeps its cut exact (every job ends on a BFS) and
+    // solves from zero flow by static push-pull
+    if (g->opt.mode == MF_MODE_PUSH_PULL) {
+        jb.exact_exit = 1;
+        jb.sink_sat = 1;
+    }
     const void *fn = job.pp ? (const void *)k_solve<true> : (const void *)k_solve<false>;
     cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(g->grid), dim3(kBlock), args, 0, st);
     if (e != cudaSuccess) {
