@@ -419,9 +419,12 @@ void mf_server_reset_stats(mf_server *s);
  * graphs stay; destroy them afterwards). */
 void mf_server_destroy(mf_server *s);
 
-/* Tracing: one record per grid barrier of the solve/repair kernel.
+/* Tracing: one record per grid barrier of the solve/repair kernel, and one
+ * per BFS level that CTA 0 ran alone (no grid barrier).
  *   phase  MF_PHASE_*; mode: BFS 0 top-down frontier, 1 top-down items of
- *          high-degree vertices, 2 bottom-up groups, 3 bottom-up items; hub
+ *          high-degree vertices, 2 bottom-up groups, 3 bottom-up items,
+ *          4 a level of a small frontier run by CTA 0 alone (not a barrier),
+ *          6 / 5 the barriers before and after such a run; hub
  *          cycles 0 set-up, 1 lowest-neighbour scan, 3 pushes;
  *          RemoveInvalidEdges: why the loop went on to another BFS, bits
  *          1 the activation rounds reached their cap, 2 the hub cycles

@@ -66,6 +66,8 @@ constexpr int kMinHubCycles = 4;
 // PushRelabel passes per loop iteration (hub cycles, then activation rounds;
 // a pass that turns hubs active again hands them to the next pass)
 constexpr int kMaxPasses = 2;
+// BFS levels whose frontier has at most this many arcs run on CTA 0 alone
+constexpr long long kSoloArcs = 8192;
 constexpr int kPassHubs = 32;   // most re-activated hubs a further pass takes
 
 constexpr int S_COUNT_MAX = 24;
@@ -112,6 +114,8 @@ struct Ctl {
     int heights_exact;    // h is the BFS fixed point of the current residual graph
     int cut_exact;        // {h >= n} is exactly the set that cannot reach a sink
     int exit_kind;        // ExitKind of the last solve/repair
+    int solo_L;           // BFS level at which CTA 0 hands a small-frontier run back
+    long long solo_seen;  // frontier arcs counted up to that level
     long long st[S_COUNT_MAX];  // statistics, see enum Stat
     long long st_aux[S_COUNT_MAX];  // where a JOB_REFRESH counts, keeping st intact
 };
@@ -986,6 +990,22 @@ __device__ __forceinline__ long long hub_move_item(const DevGraph &G, int a0, in
         }                                                                     \
     } while (0)
 #define MF_SYNC(bucket) MF_SYNC_T(bucket, -1, 0, -1)
+// The same record without a grid barrier (levels CTA 0 runs alone).
+#define MF_TRACE_T(bucket, step, mode, aux)                                   \
+    do {                                                                      \
+        if (gtid == 0) {                                                      \
+            const unsigned long long now_ = gtimer();                         \
+            const long long dt_ = (long long)(now_ - tprev);                  \
+            ST[bucket] += dt_;                                                \
+            if (TR) {                                                         \
+                const int k_ = C->trace_n++;                                  \
+                if (k_ < G.trace_cap)                                         \
+                    TR[k_] = TraceRec{(short)(bucket), (short)(mode),         \
+                                      (int)it, (int)(step), (int)(aux), dt_}; \
+            }                                                                 \
+            tprev = now_;                                                     \
+        }                                                                     \
+    } while (0)
 
 // PP: the instance that can run Dynamic Push-Pull (Alg. 8); the plain
 // instance compiles without its code paths.
@@ -1269,6 +1289,86 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             arcs_seen += mf;
             if (!bottom_up) bottom_up = mf * 14 > G.A - arcs_seen && cur * 64LL > n;
             else bottom_up = cur * 24LL >= n;
+            const bool dual = PP && stage == 1;   // push-pull: backward on T, forward on S
+            if (!bottom_up && mf <= kSoloArcs) {
+                // A small frontier: CTA 0 runs the levels alone, in step by
+                // __syncthreads only, until the frontier's arcs pass kSoloArcs,
+                // the search would turn bottom-up, or the frontier empties;
+                // the rest of the grid waits at one barrier.  Every thread has
+                // read this level's counters before CTA 0 starts to rotate
+                // them (the first barrier).
+                MF_SYNC_T(S_T_BFS, L, 6, cur);
+                if (blockIdx.x == 0) {
+                    const int cw = threadIdx.x >> 5;
+                    int Ls = L, cs = cur;
+                    long long seen = arcs_seen, mfs = 0;
+                    for (;;) {
+                        const int *Fs = (Ls & 1) ? G.qb1 : G.qb0;
+                        int *NFs = (Ls & 1) ? G.qb0 : G.qb1;
+                        int *ncs = &C->qcnt[(Ls + 1) % 3];
+                        int *ccs = &C->ccnt[Ls % 3];
+                        long long *as = &C->asum[(Ls + 1) % 3];
+                        if (threadIdx.x == 0) {
+                            C->qcnt[(Ls + 2) % 3] = 0;
+                            C->ccnt[(Ls + 1) % 3] = 0;
+                            C->gtk[(Ls + 1) % 3] = 0;
+                            C->ctk[(Ls + 1) % 3] = 0;
+                            C->asum[(Ls + 2) % 3] = 0;
+                        }
+                        for (int grp = cw; grp * 32 < cs; grp += kBlock / 32) {
+                            const int idx = grp * 32 + lane;
+                            int beg = 0, deg = 0;
+                            bool fwd = false;
+                            if (idx < cs) {
+                                const int u = lcg(&Fs[idx]);
+                                fwd = dual && G.part[u] == kPartS;
+                                beg = __ldg(&G.row[u]);
+                                deg = __ldg(&G.row[u + 1]) - beg;
+                                if (deg > kBigDeg) {
+                                    const int nc = (deg + kChunk - 1) / kChunk;
+                                    const int pos = atomicAdd(ccs, nc);
+                                    for (int c = 0; c < nc; ++c) G.cb[pos + c] = make_int2(u, beg + c * kChunk);
+                                    deg = 0;
+                                }
+                            }
+                            bfs_expand_warp(G, beg, deg, fwd, dual, Ls, ncs, NFs, as, K);
+                        }
+                        __syncthreads();
+                        const int nch = lcg(ccs);
+                        for (int c = cw; c < nch; c += kBlock / 32) {
+                            const int2 item = lcg(&G.cb[c]);
+                            const unsigned fw = (dual && G.part[item.x] == kPartS) ? (1u << kIlp) - 1u : 0u;
+                            const int a1 = min(item.y + kChunk, __ldg(&G.row[item.x + 1]));
+                            for (int ab = item.y; ab < a1; ab += 32 * kIlp) {
+                                int a[kIlp];
+                                bool ok[kIlp];
+#pragma unroll
+                                for (int j = 0; j < kIlp; ++j) {
+                                    a[j] = ab + 32 * j + lane;
+                                    ok[j] = a[j] < a1;
+                                }
+                                bfs_visit_n(G, a, ok, fw, dual, Ls, ncs, NFs, as, K);
+                            }
+                        }
+                        __syncthreads();
+                        MF_TRACE_T(S_T_BFS, Ls, 4, cs);
+                        ++Ls;
+                        cs = lcg(&C->qcnt[Ls % 3]);
+                        if (cs == 0) break;
+                        mfs = lcg(&C->asum[Ls % 3]);
+                        if (mfs > kSoloArcs || (mfs * 14 > G.A - (seen + mfs) && cs * 64LL > n)) break;
+                        seen += mfs;
+                    }
+                    if (threadIdx.x == 0) {
+                        C->solo_L = Ls;
+                        C->solo_seen = seen;   // arcs of the levels run, without level Ls
+                    }
+                }
+                MF_SYNC_T(S_T_BFS, L, 5, cur);
+                L = lcg(&C->solo_L);
+                arcs_seen = lcg(&C->solo_seen);
+                continue;
+            }
             const int *F = (L & 1) ? G.qb1 : G.qb0;
             int *NF = (L & 1) ? G.qb0 : G.qb1;
             int *ncnt = &C->qcnt[(L + 1) % 3];
@@ -1282,7 +1382,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 C->asum[(L + 2) % 3] = 0;
                 if (bottom_up) ST[S_BU_LEVELS] += 1;
             }
-            const bool dual = PP && stage == 1;   // push-pull: backward on T, forward on S
             if (bottom_up) {
                 // groups of 32 consecutive vertex ids (warp w first, then tickets)
                 const int groups = (n + 31) / 32;
@@ -1492,7 +1591,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                                     }
                                 }
                                 G.hmode[i] = mode;
-                                if (mode >= 0) atomicAdd(&C->hub_act[c & 1], 1);
+                                // a relabelled hub stays active; a pushing hub
+                                // is counted by H3 if it is still active after
+                                // its pushes
+                                if (mode == 0) atomicAdd(&C->hub_act[c & 1], 1);
                                 decided = mode;
                                 // a relabelled hub's items join the iteration's
                                 // RemoveInvalidEdges list once
@@ -1500,22 +1602,23 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                                     relabelled = false;
                             }
                         }
-                        // a hub that stays active takes all its items into the
-                        // next cycle's list, written by the warp that decided it
+                        // a relabelled hub takes all its items into the next
+                        // cycle's list, written by the warp that decided it (a
+                        // pushing hub is listed by its last H3 item, below)
                         decided = __shfl_sync(kFull, decided, 0);
                         relabelled = __shfl_sync(kFull, relabelled, 0);
-                        if (decided >= 0 || relabelled) {
+                        if (decided == 0 || relabelled) {
                             const int nit = lcg(&G.hnit[i]);
                             int pos = 0, rpos = 0;
                             if (lane == 0) {
-                                if (decided >= 0) pos = atomicAdd(&C->hlc[c & 1], nit);
+                                if (decided == 0) pos = atomicAdd(&C->hlc[c & 1], nit);
                                 if (relabelled) rpos = atomicAdd(&C->rhcnt, nit);
                             }
                             pos = __shfl_sync(kFull, pos, 0);
                             rpos = __shfl_sync(kFull, rpos, 0);
                             int2 *next_items = c & 1 ? G.hlv1 : G.hlv0;
                             for (int q = lane; q < nit; q += 32) {
-                                if (decided >= 0) next_items[pos + q] = make_int2(i, beg + q * kPrChunk);
+                                if (decided == 0) next_items[pos + q] = make_int2(i, beg + q * kPrChunk);
                                 if (relabelled) G.hri[rpos + q] = make_int2(u, beg + q * kPrChunk);
                             }
                         }
@@ -1534,22 +1637,48 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     if (gtid == 0) C->hlc[(c + 1) & 1] = 0;
                     for (int w = gwarp; w < nitems; w += nwarps) {
                         const int2 item = lcg(&items[w]);
-                        const int mode = lcg(&G.hmode[item.x]);
+                        const int i = item.x;
+                        const int mode = lcg(&G.hmode[i]);
                         if (mode <= 0) continue;
-                        if (lcg(reinterpret_cast<const int *>(&G.hikey[w])) != mode - 1) continue;  // no arc at h^ here
                         const int hh = mode - 1;
-                        const int u = lcg(&HL[item.x]);
+                        const int u = lcg(&HL[i]);
+                        const int beg = __ldg(&G.row[u]);
                         const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
                         const unsigned char side = stage == 1 ? G.part[u] : kPartT;
-                        const unsigned char *ptc = stage == 1 ? G.part : nullptr;
-                        if (PP && side == kPartS) {
-                            const long long got = hub_move_item<true>(G, item.y, a1, hh, &G.hrem[item.x], AL0, ptc,
-                                                                      side, K);
-                            if (lane == 0 && got) add_ll(&G.e[u], got);
-                        } else {
-                            const long long sent = hub_move_item<false>(G, item.y, a1, hh, &G.hrem[item.x], AL0,
-                                                                        ptc, side, K);
-                            if (lane == 0 && sent) add_ll(&G.e[u], -sent);
+                        const bool pull = PP && side == kPartS;
+                        if (lcg(reinterpret_cast<const int *>(&G.hikey[w])) == hh) {   // else no arc at h^ here
+                            const unsigned char *ptc = stage == 1 ? G.part : nullptr;
+                            if (pull) {
+                                const long long got = hub_move_item<true>(G, item.y, a1, hh, &G.hrem[i], AL0, ptc,
+                                                                          side, K);
+                                if (lane == 0 && got) add_ll(&G.e[u], got);
+                            } else {
+                                const long long sent = hub_move_item<false>(G, item.y, a1, hh, &G.hrem[i], AL0,
+                                                                            ptc, side, K);
+                                if (lane == 0 && sent) add_ll(&G.e[u], -sent);
+                            }
+                        }
+                        // the hub's last item to finish sees e(u) after all of
+                        // its pushes: a hub still active takes its items into
+                        // the next cycle's list
+                        int pos = -1;
+                        const int nit = lcg(&G.hnit[i]);
+                        if (lane == 0) {
+                            __threadfence();
+                            if (atomicAdd(&G.hdone[i], 1) == nit - 1) {
+                                __threadfence();
+                                G.hdone[i] = 0;
+                                const long long eu = lcg(&G.e[u]);
+                                if (lcg(&G.h[u]) < n && (pull ? eu < 0 : eu > 0)) {
+                                    atomicAdd(&C->hub_act[c & 1], 1);
+                                    pos = atomicAdd(&C->hlc[c & 1], nit);
+                                }
+                            }
+                        }
+                        pos = __shfl_sync(kFull, pos, 0);
+                        if (pos >= 0) {
+                            int2 *next_items = c & 1 ? G.hlv1 : G.hlv0;
+                            for (int q = lane; q < nit; q += 32) next_items[pos + q] = make_int2(i, beg + q * kPrChunk);
                         }
                     }
                     MF_SYNC_T(S_T_HUB, c, 3, lcg(&C->hub_act[c & 1]));

@@ -307,7 +307,8 @@ def test_full_size_rmat20_bench_batches(mf):
 
 
 def test_trace_records(mf):
-    """Tracing: one record per grid barrier, phases in order, BFS levels counted."""
+    """Tracing: one record per grid barrier plus one per BFS level that CTA 0
+    ran alone (mode 4), phases in order, BFS levels counted."""
     g = gen.rmat(scale=12, seed=31)
     cap = g.cap.copy()
     G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t)
@@ -316,16 +317,18 @@ def test_trace_records(mf):
     f = G.flow_value()
     recs = G.trace()
     st = G.stats()
-    assert len(recs) == st["barriers"] > 0
+    solo = [r for r in recs if r["phase"] == "bfs" and r["mode"] == 4]
+    assert len(recs) == st["barriers"] + len(solo) > 0
     assert {r["phase"] for r in recs} >= {"batch", "height_init", "bfs"}
-    bfs = [r for r in recs if r["phase"] == "bfs" and r["mode"] in (0, 2)]
+    bfs = [r for r in recs if r["phase"] == "bfs" and r["mode"] in (0, 2, 4)]
     assert len(bfs) == st["bfs_levels"]
     assert all(r["ns"] >= 0 for r in recs)
     b = gen.mixed_batch(cap, 200, 1, 500, seed=31, index=0)
     G.apply_updates(b.edge_id, b.new_cap)
     gen.apply_batch(cap, b)
     assert G.flow_value() == oracle_flow(g, cap)
-    assert len(G.trace()) == G.stats()["barriers"]
+    recs = G.trace()
+    assert len(recs) == G.stats()["barriers"] + sum(r["phase"] == "bfs" and r["mode"] == 4 for r in recs)
     G.trace_enable(0)
     assert f >= 0
     G.close()
