@@ -1516,9 +1516,19 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     if (lane == 0) {
                         pos = atomicAdd(&C->hccnt, nc);
                         G.hkey[i] = ~0ull;
-                        G.hmode[i] = 0;
                         G.hnit[i] = nc;
                         G.hdone[i] = 0;
+                        if (pass == 0) {
+                            // right after the BFS a reached vertex's lowest
+                            // residual neighbour sits exactly one level below
+                            // it, so the first cycle's decision needs no scan:
+                            // push to the arcs at height h(u) - 1
+                            const long long eu = lcg(&G.e[u]);
+                            G.hmode[i] = lcg(&G.h[u]);
+                            G.hrem[i] = eu < 0 ? -eu : eu;
+                        } else {
+                            G.hmode[i] = 0;
+                        }
                     }
                     pos = __shfl_sync(kFull, pos, 0);
                     for (int c = lane; c < nc; c += 32) G.hcl[pos + c] = make_int2(i, beg + c * kPrChunk);
@@ -1528,6 +1538,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 const int hub_cycles = kc > kMinHubCycles ? kc : kMinHubCycles;
                 for (int c = 0; c < hub_cycles; ++c) {
                     if (gtid == 0) ST[S_HUB_CYCLES] += 1;
+                    const bool fresh = c == 0 && pass == 0;   // H1 decided by the BFS heights
                     // H1: lowest residual neighbour of every unfinished hub; the
                     // warp that completes a hub's last item takes the hub's
                     // decision (push at the lowest height, relabel, or finish)
@@ -1535,7 +1546,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     // items of the hubs still active after the previous cycle
                     const int2 *items = c == 0 ? G.hcl : ((c - 1) & 1 ? G.hlv1 : G.hlv0);
                     const int nitems = c == 0 ? nhc : lcg(&C->hlc[(c - 1) & 1]);
-                    for (int w = gwarp; w < nitems; w += nwarps) {
+                    for (int w = fresh ? nitems : gwarp; w < nitems; w += nwarps) {
                         const int2 item = lcg(&items[w]);
                         const int i = item.x;
                         if (lcg(&G.hmode[i]) < 0) continue;
@@ -1623,13 +1634,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             }
                         }
                     }
-                    MF_SYNC_T(S_T_HUB, c, 1, nitems);
+                    if (!fresh) MF_SYNC_T(S_T_HUB, c, 1, nitems);
                     // hub_act[(c+1)&1] was last read by the exit test of cycle c-1,
                     // which every thread has passed once it is past the H1 barrier;
-                    // likewise the item count of the set-up, read before H1
+                    // likewise the item count of the set-up, read before H1 (with
+                    // no H1 barrier, it is zeroed after the H3 barrier instead)
                     if (gtid == 0) {
                         C->hub_act[(c + 1) & 1] = 0;
-                        if (c == 0) C->hccnt = 0;
+                        if (c == 0 && !fresh) C->hccnt = 0;
                     }
                     // H3: pushes along the lowest arcs; each warp reserves its share
                     // of the hub's excess with one atomic
@@ -1646,7 +1658,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
                         const unsigned char side = stage == 1 ? G.part[u] : kPartT;
                         const bool pull = PP && side == kPartS;
-                        if (lcg(reinterpret_cast<const int *>(&G.hikey[w])) == hh) {   // else no arc at h^ here
+                        // (hikey: the item's lowest height, found by H1; else no arc at h^ here)
+                        if (fresh || lcg(reinterpret_cast<const int *>(&G.hikey[w])) == hh) {
                             const unsigned char *ptc = stage == 1 ? G.part : nullptr;
                             if (pull) {
                                 const long long got = hub_move_item<true>(G, item.y, a1, hh, &G.hrem[i], AL0, ptc,
@@ -1682,6 +1695,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         }
                     }
                     MF_SYNC_T(S_T_HUB, c, 3, lcg(&C->hub_act[c & 1]));
+                    if (gtid == 0 && fresh) C->hccnt = 0;
                     if (lcg(&C->hub_act[c & 1]) == 0) {
                         pass_hubs_clean = true;
                         break;
