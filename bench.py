@@ -17,6 +17,8 @@ e2e        the same through the C ABI with pinned HOST batch buffers: the
            flow value and status are inside the timed region
 sizes      dynamic repair vs static GPU recompute (solve from zero flow on the
            same capacities) for 1k / 10k / 100k / 1M-edge batches
+config1    the small configuration (1,000 vertices, 50-update batches) over 100
+           seeds, every value checked against the CPU oracle
 grid       the same comparison on the 4096^2 segmentation grid with
            rectangle batches (terminal-capacity rewrites)
 serving    the request loop over eight resident graphs at two offered rates
@@ -271,6 +273,51 @@ def serving_measurement(rates, duration_s: float, seed: int = 5) -> dict:
         G.close()
     return {"graphs": SERVE_GRAPHS, "setup_s": round(t_setup, 1), "runs": runs,
             "final_values_equal_static_recompute": exact}
+
+
+def config1_measurement(seeds: int = 100) -> dict:
+    """The small configuration: 1,000-vertex / 8,000-edge random graphs (caps
+    U[1,100], a guaranteed s-t path), one static solve, then one 50-update
+    mixed batch (25 x +U[1,50], 25 x -U[1,50] clamped) and a dynamic re-solve,
+    over `seeds` seeds.  Every value is checked against the CPU oracle; the
+    graphs fit in L2, so only latencies are reported (device time, median)."""
+    import oracle
+    import torch
+    from paper_2511_05895_gb300 import MaxFlowGraph
+    stream = torch.cuda.current_stream()
+    empty = torch.zeros(0, dtype=torch.int32, device="cuda")
+    dyn, sta, orc, exact = [], [], [], True
+    for seed in range(seeds):
+        g = gen.random_graph(seed=seed)
+        cap = g.cap.copy()
+        G = MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t)
+        G.solve()
+        G.flow_value()
+        b = gen.mixed_batch(cap, 50, 1, 50, seed=seed, index=0)
+        gen.apply_batch(cap, b)
+        ids, cp = torch.from_numpy(b.edge_id).cuda(), torch.from_numpy(b.new_cap).cuda()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        G.apply_updates(ids, cp)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        f = G.flow_value()
+        ev[2].record(stream)
+        G.apply_updates(empty, empty, recompute=True)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        t0 = time.perf_counter()
+        want = oracle.maxflow_fifo(g.n, g.row_ptr, g.col, cap, g.s, g.t)
+        orc.append(time.perf_counter() - t0)
+        exact = exact and f == want == G.flow_value()
+        dyn.append(ev[0].elapsed_time(ev[1]))
+        sta.append(ev[2].elapsed_time(ev[3]))
+        G.close()
+    d, s_ = statistics.median(dyn), statistics.median(sta)
+    return {"workload": "random graphs n=1000 m=8000 caps U[1,100], one 50-update mixed batch each",
+            "seeds": seeds, "dynamic_ms": round(d, 4), "static_recompute_ms": round(s_, 4),
+            "speedup": round(s_ / d, 3), "oracle_ms_one_core": round(1000 * statistics.median(orc), 3),
+            "values_equal_oracle": exact}
 
 
 def grid_measurement(batches: int, flush, peak: float, seed: int = 3) -> dict:
@@ -596,6 +643,8 @@ def main():
     if pp is not None:
         pp["hbm_frac_of_measured"] = round(pp["algorithmic_bytes_per_launch"] / (pp["ms_per_step"] * 1e-3) / 1e9 / peak, 4)
 
+    config1 = config1_measurement() if rank == 0 and not args.no_sizes else None
+
     grid = None
     if not args.no_grid and rank == 0:
         grid = grid_measurement(5, flush, peak)
@@ -635,6 +684,7 @@ def main():
         "cpu_baseline": cpu,
         "checks": {"flow_initial": flow0, "flow_final": flow_after, "certified": certified},
         "push_pull": pp,
+        "config1": config1,
         "grid": grid,
         "serving": serving,
     }

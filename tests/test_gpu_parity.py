@@ -470,3 +470,75 @@ def test_push_pull_mode(mf, case):
             certify_gpu(G, g, cap, f)
     assert set(kinds) <= {2, 3} and 3 in kinds, kinds
     G.close()
+
+
+def test_push_pull_with_every_entry_point(mf):
+    """A push-pull graph through the other entry points: MF_DELTA, device
+    batches, a pure-increment batch off the cut (fast path), a static
+    recompute, checkpoint/resume into another push-pull graph, and the
+    learned policy -- every value the oracle's, states certified."""
+    import torch
+    g = gen.rmat(scale=12, seed=84)
+    cap = g.cap.copy()
+    PP = mf.MF_MODE_PUSH_PULL
+    G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t, mode=PP)
+    G.solve()
+    f = G.flow_value()
+    assert f == oracle_flow(g, cap)
+    # signed changes
+    b = gen.mixed_batch(cap, 300, 1, 100, seed=84, index=0)
+    delta = (b.new_cap.astype(np.int64) - cap[b.edge_id]).astype(np.int32)
+    G.apply_updates(b.edge_id, delta, delta=True)
+    gen.apply_batch(cap, b)
+    assert G.flow_value() == oracle_flow(g, cap) and G.stats()["exit_kind"] == 3
+    # device batch
+    b = gen.mixed_batch(cap, 300, 1, 100, seed=84, index=1)
+    G.apply_updates(torch.from_numpy(b.edge_id).cuda(), torch.from_numpy(b.new_cap).cuda())
+    gen.apply_batch(cap, b)
+    f = G.flow_value()
+    assert f == oracle_flow(g, cap)
+    # increments off the exact cut: no loop, value unchanged
+    side = G.min_cut()
+    tails = g.tails()
+    off = np.flatnonzero(~((side[tails] == 1) & (side[g.col] == 0)))
+    ids = np.sort(np.random.default_rng(84).choice(off, 200, replace=False)).astype(np.int32)
+    new = (cap[ids].astype(np.int64) + 7).astype(np.int32)
+    G.apply_updates(ids, new)
+    cap[ids] = new
+    assert G.flow_value() == f == oracle_flow(g, cap) and G.stats()["exit_kind"] == 2
+    # a push-pull repair right after the fast path, then a static recompute
+    b = gen.mixed_batch(cap, 300, 1, 100, seed=84, index=2)
+    G.apply_updates(b.edge_id, b.new_cap)
+    gen.apply_batch(cap, b)
+    assert G.flow_value() == oracle_flow(g, cap) and G.stats()["exit_kind"] == 3
+    b = gen.mixed_batch(cap, 300, 1, 100, seed=84, index=3)
+    G.apply_updates(b.edge_id, b.new_cap, recompute=True)
+    gen.apply_batch(cap, b)
+    f = G.flow_value()
+    assert f == oracle_flow(g, cap)
+    certify_gpu(G, g, cap, f)
+    # checkpoint into a fresh push-pull graph: its first repair falls back to
+    # the plain loop (no exact cut yet), the next ones are push-pull again
+    r, e, h = G.export_state()
+    H = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t, mode=PP)
+    H.import_state(r, e, h)
+    kinds = []
+    for i in range(4, 7):
+        b = gen.mixed_batch(cap, 300, 1, 100, seed=84, index=i)
+        H.apply_updates(b.edge_id, b.new_cap)
+        gen.apply_batch(cap, b)
+        assert H.flow_value() == oracle_flow(g, cap)
+        kinds.append(H.stats()["exit_kind"])
+    assert kinds[0] != 3 and kinds[-1] == 3, kinds
+    certify_gpu(H, g, cap, H.flow_value())
+    # the learned policy on a push-pull graph
+    from paper_2511_05895_gb300.policy import load_default_params
+    H.set_policy(mf.MF_POLICY_LEARNED, load_default_params())
+    for i in range(7, 9):
+        b = gen.mixed_batch(cap, 300 if i == 7 else g.m // 10, 1, 100, seed=84, index=i)
+        H.apply_updates(b.edge_id, b.new_cap)
+        gen.apply_batch(cap, b)
+        assert H.flow_value() == oracle_flow(g, cap)
+    certify_gpu(H, g, cap, H.flow_value())
+    G.close()
+    H.close()

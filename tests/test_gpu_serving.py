@@ -126,6 +126,28 @@ def test_sm_slots_serialise_and_hbm_budget_admits(mf):
     G2.close()
 
 
+def test_push_pull_graphs_in_the_server(mf):
+    """Push-pull graphs served by the request loop (captured repairs) give the
+    oracle's values."""
+    g = gen.rmat(scale=12, seed=72)
+    G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, grid_blocks=76, mode=mf.MF_MODE_PUSH_PULL)
+    G.solve()
+    G.flow_value()
+    S = mf.Server()
+    S.add_graph(G, 2000)
+    cap = g.cap.copy()
+    out = []
+    for j in range(5):
+        b = gen.mixed_batch(cap, 500, 1, 100, seed=72, index=j)
+        gen.apply_batch(cap, b)
+        out.append((S.submit(0, b.edge_id, b.new_cap), oracle.maxflow_fifo(g.n, g.row_ptr, g.col, cap, g.s, g.t)))
+    S.drain()
+    for t, want in out:
+        assert S.poll(t)[1] == want
+    S.close()
+    G.close()
+
+
 def test_cuda_graph_capture_and_recompute_requests(mf):
     g = gen.rmat(scale=12, seed=71)
     G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, grid_blocks=76)
