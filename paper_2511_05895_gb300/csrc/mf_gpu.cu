@@ -202,6 +202,15 @@ __device__ __forceinline__ void add_ll(long long *p, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
 }
 
+// Arrival on a counter with acquire-release order at GPU scope: this
+// thread's earlier writes are visible to whoever sees the new count, and the
+// last arrival sees everyone's.
+__device__ __forceinline__ int arrive_acq_rel(int *p) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -1573,9 +1582,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         if (lane == 0) {
                             G.hikey[w] = (unsigned)(best >> 32);   // lowest height in this item
                             if (best != ~0ull) atomicMin(&G.hkey[i], best);
-                            __threadfence();
-                            if (atomicAdd(&G.hdone[i], 1) == lcg(&G.hnit[i]) - 1) {
-                                __threadfence();
+                            if (arrive_acq_rel(&G.hdone[i]) == lcg(&G.hnit[i]) - 1) {
                                 const int hu = lcg(&G.h[u]);
                                 const long long eu = pull ? -lcg(&G.e[u]) : lcg(&G.e[u]);   // amount to move
                                 const unsigned long long key = __ldcg(&G.hkey[i]);
@@ -1677,9 +1684,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         int pos = -1;
                         const int nit = lcg(&G.hnit[i]);
                         if (lane == 0) {
-                            __threadfence();
-                            if (atomicAdd(&G.hdone[i], 1) == nit - 1) {
-                                __threadfence();
+                            if (arrive_acq_rel(&G.hdone[i]) == nit - 1) {
                                 G.hdone[i] = 0;
                                 const long long eu = lcg(&G.e[u]);
                                 if (lcg(&G.h[u]) < n && (pull ? eu < 0 : eu > 0)) {
