@@ -204,10 +204,11 @@ def serving_measurement(rates, duration_s: float, seed: int = 5) -> dict:
     vertices and 16M edges): for each offered rate, Poisson arrivals for
     `duration_s`, batch sizes log-uniform in [100, 100k] (grids: the pixels of
     a rectangle of that many terminal arcs), served by mf_server with per-graph
-    grids of 19 to 152 CTAs.  Reports p50/p99 submit-to-completion latency and
-    the completed batches per second at each rate."""
+    grids of 19 to 152 CTAs, every graph repaired by Dynamic Push-Pull.  Reports
+    p50/p99 submit-to-completion latency and the completed batches per second
+    at each rate."""
     from concurrent.futures import ThreadPoolExecutor
-    from paper_2511_05895_gb300 import MaxFlowGraph, Server
+    from paper_2511_05895_gb300 import MF_MODE_PUSH_PULL, MaxFlowGraph, Server
     makers = [(lambda: gen.rmat(scale=16, seed=301), 19), (lambda: gen.rmat(scale=18, seed=302), 38),
               (lambda: gen.rmat(scale=20, seed=303), 76), (lambda: gen.rmat(scale=22, seed=304), 152),
               (lambda: gen.grid_segmentation(1024, 1024, seed=305), 38),
@@ -220,7 +221,8 @@ def serving_measurement(rates, duration_s: float, seed: int = 5) -> dict:
     S = Server()
     Gs, caps = [], []
     for g, (_, grid) in zip(graphs, makers):
-        G = MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=4, grid_blocks=grid)
+        G = MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=4, grid_blocks=grid,
+                         mode=MF_MODE_PUSH_PULL)
         G.solve()
         G.flow_value()
         S.add_graph(G, 100_000)
@@ -271,7 +273,7 @@ def serving_measurement(rates, duration_s: float, seed: int = 5) -> dict:
     S.close()
     for G in Gs:
         G.close()
-    return {"graphs": SERVE_GRAPHS, "setup_s": round(t_setup, 1), "runs": runs,
+    return {"graphs": SERVE_GRAPHS, "mode": "push-pull", "setup_s": round(t_setup, 1), "runs": runs,
             "final_values_equal_static_recompute": exact}
 
 
