@@ -942,6 +942,8 @@ __device__ __forceinline__ long long hub_move_item(const DevGraph &G, int a0, in
     const int lane = threadIdx.x & 31;
     long long sent = 0;
     for (; a0 < a1; a0 += 32 * kIlp) {
+        // the hub's excess may already be reserved by the items before this one
+        if (__shfl_sync(kFull, lane == 0 ? lcg(rem) : 0ll, 0) <= 0) break;
         ArcRound R;
         load_round_t<PULL>(G, a0, a1, R, pt, side);
         K.pr_arcs += round_arcs(a0, a1);
