@@ -938,12 +938,14 @@ __device__ __forceinline__ unsigned long long hub_scan_item(const DevGraph &G, i
 template <bool PULL>
 __device__ __forceinline__ long long hub_move_item(const DevGraph &G, int a0, int a1, int hh, long long *rem,
                                                    const ActList &AL, const unsigned char *pt, unsigned char side,
-                                                   Counters &K) {
+                                                   bool skip_done, Counters &K) {
     const int lane = threadIdx.x & 31;
     long long sent = 0;
     for (; a0 < a1; a0 += 32 * kIlp) {
-        // the hub's excess may already be reserved by the items before this one
-        if (__shfl_sync(kFull, lane == 0 ? lcg(rem) : 0ll, 0) <= 0) break;
+        // the hub's excess may already be reserved by the items before this
+        // one (not checked in the first push-pull stage, where scanning every
+        // item measured faster: its pushes spread over the hub's arcs)
+        if (skip_done && __shfl_sync(kFull, lane == 0 ? lcg(rem) : 0ll, 0) <= 0) break;
         ArcRound R;
         load_round_t<PULL>(G, a0, a1, R, pt, side);
         K.pr_arcs += round_arcs(a0, a1);
@@ -1672,11 +1674,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             const unsigned char *ptc = stage == 1 ? G.part : nullptr;
                             if (pull) {
                                 const long long got = hub_move_item<true>(G, item.y, a1, hh, &G.hrem[i], AL0, ptc,
-                                                                          side, K);
+                                                                          side, stage != 1, K);
                                 if (lane == 0 && got) add_ll(&G.e[u], got);
                             } else {
                                 const long long sent = hub_move_item<false>(G, item.y, a1, hh, &G.hrem[i], AL0,
-                                                                            ptc, side, K);
+                                                                            ptc, side, stage != 1, K);
                                 if (lane == 0 && sent) add_ll(&G.e[u], -sent);
                             }
                         }
