@@ -60,10 +60,14 @@ def test_config1_random_graph(mf, seed):
     G.close()
 
 
-def test_tiny_graphs_many(mf):
+@pytest.mark.parametrize("mode", ["data-driven", "push-pull"])
+def test_tiny_graphs_many(mf, mode):
     """Hundreds of tiny graphs with ties, zero caps, self-loops, parallel and
-    antiparallel edges; every state certified."""
-    rng = np.random.default_rng(2024)
+    antiparallel edges, in the data-driven and the push-pull mode (empty and
+    one-vertex subgraphs P, s next to t, unreachable t); every state
+    certified."""
+    opts = {"mode": mf.MF_MODE_PUSH_PULL} if mode == "push-pull" else {}
+    rng = np.random.default_rng(2024 if mode == "data-driven" else 2025)
     for trial in range(150):
         n = int(rng.integers(2, 24))
         m = int(rng.integers(1, 4 * n + 1))
@@ -79,7 +83,7 @@ def test_tiny_graphs_many(mf):
                 k = int(r.integers(0, m + 1))
                 ids = r.choice(m, k, replace=False).astype(np.int32)
                 yield gen.Batch(edge_id=ids, new_cap=r.integers(0, 7, k).astype(np.int32))
-        G, _ = run_batches(mf, g, batches)
+        G, _ = run_batches(mf, g, batches, **opts)
         G.close()
 
 
