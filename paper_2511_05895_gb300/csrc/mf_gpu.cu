@@ -66,8 +66,10 @@ constexpr int kMinHubCycles = 4;
 // PushRelabel passes per loop iteration (hub cycles, then activation rounds;
 // a pass that turns hubs active again hands them to the next pass)
 constexpr int kMaxPasses = 2;
-// BFS levels whose frontier has at most this many arcs run on CTA 0 alone
+// BFS levels whose frontier has at most this many arcs and vertices run on
+// CTA 0 alone, with the frontiers in shared memory
 constexpr long long kSoloArcs = 8192;
+constexpr int kSoloCap = 4096;
 constexpr int kPassHubs = 32;   // most re-activated hubs a further pass takes
 
 constexpr int S_COUNT_MAX = 24;
@@ -313,8 +315,10 @@ struct ArcRoundBfs {
 };
 
 // Warp-aggregated append of the lanes' flagged values of kIlp slots: one
-// atomicAdd for the whole warp and all slots.  All 32 lanes call.
-__device__ __forceinline__ void warp_append_n(const bool (&pred)[kIlp], const int (&val)[kIlp], int *cnt, int *buf) {
+// atomicAdd for the whole warp and all slots; positions from cap on go to
+// spill (same positions) instead of buf.  All 32 lanes call.
+__device__ __forceinline__ void warp_append_n(const bool (&pred)[kIlp], const int (&val)[kIlp], int *cnt, int *buf,
+                                              int cap = 0x7fffffff, int *spill = nullptr) {
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     unsigned m[kIlp];
@@ -330,7 +334,10 @@ __device__ __forceinline__ void warp_append_n(const bool (&pred)[kIlp], const in
     base = __shfl_sync(kFull, base, 0);
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) {
-        if (pred[j]) buf[base + __popc(m[j] & below)] = val[j];
+        if (pred[j]) {
+            const int pos = base + __popc(m[j] & below);
+            (pos < cap ? buf : spill)[pos] = val[j];
+        }
         base += __popc(m[j]);
     }
 }
@@ -339,12 +346,12 @@ __device__ __forceinline__ void warp_append_n(const bool (&pred)[kIlp], const in
 // issued together and each list gets one reservation per warp.
 __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (&disc)[kIlp], const int (&v)[kIlp],
                                                  unsigned fwd, bool dual, int *ncnt, int *NF, long long *asum,
-                                                 Counters &K) {
+                                                 Counters &K, int cap = 0x7fffffff, int *spill = nullptr) {
     bool any = false;
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) any |= disc[j];
     if (!__any_sync(kFull, any)) return;
-    warp_append_n(disc, v, ncnt, NF);
+    warp_append_n(disc, v, ncnt, NF, cap, spill);
     int deg[kIlp];
     long long ev[kIlp];
 #pragma unroll
@@ -404,7 +411,7 @@ __device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int
 // issued before any of them is used.  All 32 lanes call.
 __device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kIlp], const bool (&ok)[kIlp],
                                             unsigned fwd, bool dual, int L, int *ncnt, int *NF, long long *asum,
-                                            Counters &K) {
+                                            Counters &K, int cap = 0x7fffffff, int *spill = nullptr) {
     const int n = G.n;
     int v[kIlp], rin[kIlp], hv[kIlp];
     bool disc[kIlp];
@@ -418,7 +425,7 @@ __device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kI
     for (int j = 0; j < kIlp; ++j) hv[j] = (rin[j] > 0 && v[j] != G.s) ? lcg(&G.h[v[j]]) : -1;
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) disc[j] = hv[j] == n && atomicCAS(&G.h[v[j]], n, L + 1) == n;
-    bfs_discovered_n(G, disc, v, fwd, dual, ncnt, NF, asum, K);
+    bfs_discovered_n(G, disc, v, fwd, dual, ncnt, NF, asum, K, cap, spill);
 }
 
 // Expand up to 32 frontier vertices (one per lane, degree deg starting at
@@ -426,7 +433,8 @@ __device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kI
 // balanced over the lanes: lane i handles arcs k0 + 32 j + i of the
 // concatenated lists.
 __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int deg, bool fwd, bool dual, int L,
-                                                int *ncnt, int *NF, long long *asum, Counters &K) {
+                                                int *ncnt, int *NF, long long *asum, Counters &K,
+                                                int cap = 0x7fffffff, int *spill = nullptr) {
     const unsigned fwd_lanes = __ballot_sync(kFull, fwd);
     const int lane = threadIdx.x & 31;
     int incl = deg;
@@ -457,7 +465,7 @@ __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int 
             a[jj] = ob + (k - oe);
             fw |= ((fwd_lanes >> j) & 1u) << jj;
         }
-        bfs_visit_n(G, a, ok, fw, dual, L, ncnt, NF, asum, K);
+        bfs_visit_n(G, a, ok, fw, dual, L, ncnt, NF, asum, K, cap, spill);
     }
 }
 
@@ -1303,37 +1311,40 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             if (!bottom_up) bottom_up = mf * 14 > G.A - arcs_seen && cur * 64LL > n;
             else bottom_up = cur * 24LL >= n;
             const bool dual = PP && stage == 1;   // push-pull: backward on T, forward on S
-            if (!bottom_up && mf <= kSoloArcs) {
-                // A small frontier: CTA 0 runs the levels alone, in step by
-                // __syncthreads only, until the frontier's arcs pass kSoloArcs,
-                // the search would turn bottom-up, or the frontier empties;
-                // the rest of the grid waits at one barrier.  Every thread has
-                // read this level's counters before CTA 0 starts to rotate
-                // them (the first barrier).
+            if (!bottom_up && mf <= kSoloArcs && cur <= kSoloCap) {
+                // A small frontier: CTA 0 runs the levels alone, with the
+                // frontiers in shared memory and in step by __syncthreads only,
+                // until the frontier passes kSoloCap vertices or kSoloArcs arcs,
+                // the search would turn bottom-up, or the frontier empties; it
+                // then hands the frontier back in the global queue.  The rest
+                // of the grid waits at one barrier.  Every thread has read this
+                // level's counters before CTA 0 starts (the first barrier).
                 MF_SYNC_T(S_T_BFS, L, 6, cur);
                 if (blockIdx.x == 0) {
+                    __shared__ int s_front[2][kSoloCap];
+                    __shared__ int s_cnt[2];
+                    __shared__ long long s_arcs[2];
+                    __shared__ int s_big;
                     const int cw = threadIdx.x >> 5;
-                    int Ls = L, cs = cur;
+                    const int *F0 = (L & 1) ? G.qb1 : G.qb0;
+                    for (int i = threadIdx.x; i < cur; i += kBlock) s_front[0][i] = lcg(&F0[i]);
+                    if (threadIdx.x == 0) {
+                        s_cnt[1] = 0;
+                        s_arcs[1] = 0;
+                        s_big = 0;
+                    }
+                    __syncthreads();
+                    int Ls = L, cs = cur, b = 0;
                     long long seen = arcs_seen, mfs = 0;
                     for (;;) {
-                        const int *Fs = (Ls & 1) ? G.qb1 : G.qb0;
-                        int *NFs = (Ls & 1) ? G.qb0 : G.qb1;
-                        int *ncs = &C->qcnt[(Ls + 1) % 3];
                         int *ccs = &C->ccnt[Ls % 3];
-                        long long *as = &C->asum[(Ls + 1) % 3];
-                        if (threadIdx.x == 0) {
-                            C->qcnt[(Ls + 2) % 3] = 0;
-                            C->ccnt[(Ls + 1) % 3] = 0;
-                            C->gtk[(Ls + 1) % 3] = 0;
-                            C->ctk[(Ls + 1) % 3] = 0;
-                            C->asum[(Ls + 2) % 3] = 0;
-                        }
+                        int *spill = (Ls & 1) ? G.qb0 : G.qb1;   // positions >= kSoloCap of the next frontier
                         for (int grp = cw; grp * 32 < cs; grp += kBlock / 32) {
                             const int idx = grp * 32 + lane;
                             int beg = 0, deg = 0;
                             bool fwd = false;
                             if (idx < cs) {
-                                const int u = lcg(&Fs[idx]);
+                                const int u = s_front[b][idx];
                                 fwd = dual && G.part[u] == kPartS;
                                 beg = __ldg(&G.row[u]);
                                 deg = __ldg(&G.row[u + 1]) - beg;
@@ -1341,38 +1352,62 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                                     const int nc = (deg + kChunk - 1) / kChunk;
                                     const int pos = atomicAdd(ccs, nc);
                                     for (int c = 0; c < nc; ++c) G.cb[pos + c] = make_int2(u, beg + c * kChunk);
+                                    s_big = 1;
                                     deg = 0;
                                 }
                             }
-                            bfs_expand_warp(G, beg, deg, fwd, dual, Ls, ncs, NFs, as, K);
+                            bfs_expand_warp(G, beg, deg, fwd, dual, Ls, &s_cnt[b ^ 1], s_front[b ^ 1],
+                                            &s_arcs[b ^ 1], K, kSoloCap, spill);
                         }
                         __syncthreads();
-                        const int nch = lcg(ccs);
-                        for (int c = cw; c < nch; c += kBlock / 32) {
-                            const int2 item = lcg(&G.cb[c]);
-                            const unsigned fw = (dual && G.part[item.x] == kPartS) ? (1u << kIlp) - 1u : 0u;
-                            const int a1 = min(item.y + kChunk, __ldg(&G.row[item.x + 1]));
-                            for (int ab = item.y; ab < a1; ab += 32 * kIlp) {
-                                int a[kIlp];
-                                bool ok[kIlp];
+                        if (s_big) {
+                            const int nch = lcg(ccs);
+                            for (int c = cw; c < nch; c += kBlock / 32) {
+                                const int2 item = lcg(&G.cb[c]);
+                                const unsigned fw = (dual && G.part[item.x] == kPartS) ? (1u << kIlp) - 1u : 0u;
+                                const int a1 = min(item.y + kChunk, __ldg(&G.row[item.x + 1]));
+                                for (int ab = item.y; ab < a1; ab += 32 * kIlp) {
+                                    int a[kIlp];
+                                    bool ok[kIlp];
 #pragma unroll
-                                for (int j = 0; j < kIlp; ++j) {
-                                    a[j] = ab + 32 * j + lane;
-                                    ok[j] = a[j] < a1;
+                                    for (int j = 0; j < kIlp; ++j) {
+                                        a[j] = ab + 32 * j + lane;
+                                        ok[j] = a[j] < a1;
+                                    }
+                                    bfs_visit_n(G, a, ok, fw, dual, Ls, &s_cnt[b ^ 1], s_front[b ^ 1],
+                                                &s_arcs[b ^ 1], K, kSoloCap, spill);
                                 }
-                                bfs_visit_n(G, a, ok, fw, dual, Ls, ncs, NFs, as, K);
                             }
+                            __syncthreads();
                         }
-                        __syncthreads();
                         MF_TRACE_T(S_T_BFS, Ls, 4, cs);
                         ++Ls;
-                        cs = lcg(&C->qcnt[Ls % 3]);
-                        if (cs == 0) break;
-                        mfs = lcg(&C->asum[Ls % 3]);
-                        if (mfs > kSoloArcs || (mfs * 14 > G.A - (seen + mfs) && cs * 64LL > n)) break;
+                        cs = s_cnt[b ^ 1];
+                        mfs = s_arcs[b ^ 1];
+                        __syncthreads();   // everyone has read the counts
+                        b ^= 1;
+                        if (threadIdx.x == 0) {
+                            s_cnt[b ^ 1] = 0;
+                            s_arcs[b ^ 1] = 0;
+                            s_big = 0;
+                            C->ccnt[Ls % 3] = 0;
+                        }
+                        if (cs == 0 || cs > kSoloCap || mfs > kSoloArcs ||
+                            (mfs * 14 > G.A - (seen + mfs) && cs * 64LL > n))
+                            break;
                         seen += mfs;
+                        __syncthreads();
                     }
+                    // hand the frontier of level Ls back in the global queue
+                    int *Fg = (Ls & 1) ? G.qb1 : G.qb0;
+                    for (int i = threadIdx.x; i < min(cs, kSoloCap); i += kBlock) Fg[i] = s_front[b][i];
                     if (threadIdx.x == 0) {
+                        C->qcnt[Ls % 3] = cs;
+                        C->asum[Ls % 3] = mfs;
+                        C->qcnt[(Ls + 1) % 3] = 0;
+                        C->asum[(Ls + 1) % 3] = 0;
+                        C->gtk[Ls % 3] = 0;
+                        C->ctk[Ls % 3] = 0;
                         C->solo_L = Ls;
                         C->solo_seen = seen;   // arcs of the levels run, without level Ls
                     }
