@@ -87,8 +87,14 @@ def algorithmic_bytes(st: dict, n: int) -> int:
 
 
 def kernel_source_hash() -> str:
+    """sha256[:16] of mf_gpu.cu without its comments and blank space: the
+    same hash means the same compiled kernel."""
     p = os.path.join(ROOT, "paper_2511_05895_gb300", "csrc", "mf_gpu.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    src = open(p).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = re.sub(r"\s+", " ", src)
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def recorded_traffic(kernel_hash: str):

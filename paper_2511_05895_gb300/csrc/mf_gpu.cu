@@ -13,8 +13,15 @@
 //             backward BFS global relabel + active worklist (Sec. 5.3)
 //             stop when no vertex is active
 //             PushRelabel x KERNELCYCLES (Alg. 2)
-//             RemoveInvalidEdges (Alg. 3) }
+//             RemoveInvalidEdges (Alg. 3)
+//             stop when that round left nothing pending (Alg. 4's own test) }
 //   -> flow = e(t) + sum of deficits (Alg. 4, final sum).
+//
+// Dynamic Push-Pull (Alg. 6-8) runs in the same loop, in the instance
+// k_solve<true>: saturate the arcs across the previous cut, then push on its
+// sink side and pull on its source side (one search, both heights in h), then
+// the plain loop on the leftover subgraph P.  A batch that only raises
+// capacities off the exact cut skips the loop (the flow cannot change).
 //
 // Residual capacities are kept twice: r[a] and its mirror rr[a] = r[rev[a]],
 // so that the backward BFS reads the residual of the arc INTO the frontier
