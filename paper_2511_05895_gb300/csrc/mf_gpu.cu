@@ -349,16 +349,84 @@ __device__ __forceinline__ void warp_append_n(const bool (&pred)[kIlp], const in
     }
 }
 
+constexpr int kWq = 320;   // staged frontier entries per warp (24 warps: 7680 ints)
+
+// The next BFS frontier as one warp writes it.  In grid-wide levels the
+// entries are staged in the warp's kWq ints of shared memory and reach the
+// global queue buf a whole stage at a time (one reservation on cnt), and the
+// arc total is summed in a register: the two counters every warp of the grid
+// shares then take one atomic per stage instead of one per round of arcs.
+// front_flush must run before the level's grid barrier.  In CTA 0's
+// small-frontier levels (stage == nullptr) entries go straight to the shared
+// frontier (positions >= cap to spill) and the arc total to its counter.
+struct Front {
+    int *cnt, *buf;
+    long long *asum;
+    int cap;
+    int *spill;
+    int *stage;     // this warp's kWq shared ints, or nullptr
+    int sn;         // staged entries (warp-uniform)
+    long long ds;   // arc total not yet added (warp-uniform)
+};
+
+__device__ __forceinline__ void front_flush_entries(Front &F) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    int base = 0;
+    if (lane == 0) base = atomicAdd(F.cnt, F.sn);
+    base = __shfl_sync(kFull, base, 0);
+    for (int i = lane; i < F.sn; i += 32) F.buf[base + i] = F.stage[i];
+    __syncwarp();
+    F.sn = 0;
+}
+
+// Publish what the warp has staged.  All 32 lanes call.
+__device__ __forceinline__ void front_flush(Front &F) {
+    if (F.stage && F.sn) front_flush_entries(F);
+    if (F.ds && (threadIdx.x & 31) == 0) add_ll(F.asum, F.ds);
+    F.ds = 0;
+}
+
+// Append the lanes' flagged values of kIlp slots (at most 32 kIlp <= kWq
+// entries).  All 32 lanes call.
+__device__ __forceinline__ void front_append_n(const bool (&pred)[kIlp], const int (&val)[kIlp], Front &F) {
+    if (!F.stage) {
+        warp_append_n(pred, val, F.cnt, F.buf, F.cap, F.spill);
+        return;
+    }
+    const unsigned below = (1u << (threadIdx.x & 31)) - 1u;
+    unsigned m[kIlp];
+    int tot = 0;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        m[j] = __ballot_sync(kFull, pred[j]);
+        tot += __popc(m[j]);
+    }
+    if (tot == 0) return;
+    if (F.sn + tot > kWq) front_flush_entries(F);
+    int base = F.sn;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        if (pred[j]) F.stage[base + __popc(m[j] & below)] = val[j];
+        base += __popc(m[j]);
+    }
+    F.sn = base;
+}
+
+__device__ __forceinline__ void front_add_arcs(Front &F, long long ds) {
+    if (F.stage) F.ds += ds;
+    else if ((threadIdx.x & 31) == 0 && ds) add_ll(F.asum, ds);
+}
+
 // bfs_discovered for kIlp slots per lane at once: the loads of all slots are
 // issued together and each list gets one reservation per warp.
 __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (&disc)[kIlp], const int (&v)[kIlp],
-                                                 unsigned fwd, bool dual, int *ncnt, int *NF, long long *asum,
-                                                 Counters &K, int cap = 0x7fffffff, int *spill = nullptr) {
+                                                 unsigned fwd, bool dual, Front &F, Counters &K) {
     bool any = false;
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) any |= disc[j];
     if (!__any_sync(kFull, any)) return;
-    warp_append_n(disc, v, ncnt, NF, cap, spill);
+    front_append_n(disc, v, F);
     int deg[kIlp];
     long long ev[kIlp];
 #pragma unroll
@@ -377,8 +445,7 @@ __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (
         hub[j] = act && deg[j] > kHubDeg;
         small[j] = act && !hub[j];
     }
-    ds = warp_sum(ds);
-    if ((threadIdx.x & 31) == 0 && ds) add_ll(asum, ds);
+    front_add_arcs(F, warp_sum(ds));
     warp_append_n(small, v, &G.ctl->wcnt, G.wl);
     warp_append_n(hub, v, &G.ctl->hcnt, G.hl);
 }
@@ -388,9 +455,15 @@ __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (
 // with positive excess it is active: worklist (degree <= kHubDeg) or hub
 // list.  All 32 lanes call.
 __device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int v, bool fwd, bool dual,
-                                               int *ncnt, int *NF, long long *asum, Counters &K) {
-    warp_append(disc, v, ncnt, NF);
+                                               Front &F, Counters &K) {
     if (!__ballot_sync(kFull, disc)) return;
+    {
+        bool p[kIlp] = {};
+        int x[kIlp] = {};
+        p[0] = disc;
+        x[0] = v;
+        front_append_n(p, x, F);
+    }
     int deg = 0;
     bool act = false;
     if (disc) {
@@ -399,8 +472,7 @@ __device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int
         act = fwd ? ev < 0 : ev > 0;
         ++K.bfs_verts;
     }
-    const long long ds = warp_sum((long long)deg);
-    if ((threadIdx.x & 31) == 0 && ds) add_ll(asum, ds);
+    front_add_arcs(F, warp_sum((long long)deg));
     if (__ballot_sync(kFull, act)) {
         const bool hub = act && deg > kHubDeg;
         warp_append(act && !hub, v, &G.ctl->wcnt, G.wl);
@@ -417,8 +489,7 @@ __device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int
 // residual (r[a] > 0), and a deficient v is active.  Every load of a round is
 // issued before any of them is used.  All 32 lanes call.
 __device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kIlp], const bool (&ok)[kIlp],
-                                            unsigned fwd, bool dual, int L, int *ncnt, int *NF, long long *asum,
-                                            Counters &K, int cap = 0x7fffffff, int *spill = nullptr) {
+                                            unsigned fwd, bool dual, int L, Front &F, Counters &K) {
     const int n = G.n;
     int v[kIlp], rin[kIlp], hv[kIlp];
     bool disc[kIlp];
@@ -432,7 +503,7 @@ __device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kI
     for (int j = 0; j < kIlp; ++j) hv[j] = (rin[j] > 0 && v[j] != G.s) ? lcg(&G.h[v[j]]) : -1;
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) disc[j] = hv[j] == n && atomicCAS(&G.h[v[j]], n, L + 1) == n;
-    bfs_discovered_n(G, disc, v, fwd, dual, ncnt, NF, asum, K, cap, spill);
+    bfs_discovered_n(G, disc, v, fwd, dual, F, K);
 }
 
 // Expand up to 32 frontier vertices (one per lane, degree deg starting at
@@ -440,8 +511,7 @@ __device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kI
 // balanced over the lanes: lane i handles arcs k0 + 32 j + i of the
 // concatenated lists.
 __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int deg, bool fwd, bool dual, int L,
-                                                int *ncnt, int *NF, long long *asum, Counters &K,
-                                                int cap = 0x7fffffff, int *spill = nullptr) {
+                                                Front &F, Counters &K) {
     const unsigned fwd_lanes = __ballot_sync(kFull, fwd);
     const int lane = threadIdx.x & 31;
     int incl = deg;
@@ -472,7 +542,7 @@ __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int 
             a[jj] = ob + (k - oe);
             fw |= ((fwd_lanes >> j) & 1u) << jj;
         }
-        bfs_visit_n(G, a, ok, fw, dual, L, ncnt, NF, asum, K, cap, spill);
+        bfs_visit_n(G, a, ok, fw, dual, L, F, K);
     }
 }
 
@@ -485,8 +555,8 @@ __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int 
 // push-pull repair (dual) a vertex of the pull side looks for a residual arc
 // w -> v from the frontier instead, and only frontier vertices of the
 // vertex's own side count.  All 32 lanes call.
-__device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base, bool dual, int L, int *ncnt,
-                                                    int *NF, long long *asum, int *ccnt, Counters &K) {
+__device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base, bool dual, int L, Front &F,
+                                                    int *ccnt, Counters &K) {
     const int lane = threadIdx.x & 31;
     const int n = G.n;
     const int v = base + lane;
@@ -544,13 +614,13 @@ __device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base,
     }
     const bool disc = (found >> lane) & 1u;
     if (disc) G.h[v] = L + 1;
-    bfs_discovered(G, disc, v, side == kPartS, dual, ncnt, NF, asum, K);
+    bfs_discovered(G, disc, v, side == kPartS, dual, F, K);
 }
 
 // Bottom-up scan of one kChunk-arc item of a high-degree unvisited vertex;
 // several items of one vertex may find a parent, the height CAS elects one.
-__device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item, bool dual, int L, int *ncnt,
-                                                   int *NF, long long *asum, Counters &K) {
+__device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item, bool dual, int L, Front &F,
+                                                   Counters &K) {
     const int lane = threadIdx.x & 31;
     const int v = item.x;
     const int side = dual ? G.part[v] : kPartT;
@@ -577,7 +647,7 @@ __device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item,
         if (hit && lane == 0) disc = atomicCAS(&G.h[v], G.n, L + 1) == G.n;
     }
     disc = __shfl_sync(kFull, disc, 0);
-    bfs_discovered(G, disc && lane == 0, v, side == kPartS, dual, ncnt, NF, asum, K);
+    bfs_discovered(G, disc && lane == 0, v, side == kPartS, dual, F, K);
 }
 
 // ------------------------------------------------------ push / relabel --
@@ -625,30 +695,44 @@ __device__ __forceinline__ void note_relabel(const DevGraph &G, int u, unsigned 
     if (atomicExch(&G.rstamp[u], rstamp) != rstamp) G.rl[atomicAdd(&G.ctl->rlcnt, 1)] = u;
 }
 
-// A push of d units raised e(v) from `old` (a pull lowered it): if v turned
-// active (excess positive -- for a pull, negative -- below height n, not s or
-// t) it joins the next activation round when its degree is <= kHubDeg, else
-// the hub list of the next PushRelabel pass.  All 32 lanes call.
+// The kIlp moves of a round (d[j] > 0: d[j] units along slot j to v[j],
+// whose excess was old[j]): a push that raised e(v) above 0 (a pull that
+// lowered it below 0) turned v active, and v (not s or t, below height n)
+// joins the next activation round when its degree is <= kHubDeg, else the
+// hub list of the next PushRelabel pass.  The loads and stamps of all slots
+// are issued together, and each list gets one reservation per warp.  All 32
+// lanes call.
 template <bool PULL>
-__device__ __forceinline__ void note_activation_t(const DevGraph &G, bool moved, int v, long long old, long long d,
-                                                  const ActList &AL) {
-    bool add = false, add_hub = false;
-    const bool turned = PULL ? (old >= 0 && old - d < 0) : (old <= 0 && old + d > 0);
-    if (moved && turned && v != G.s && v != G.t) {
-        if (lcg(&G.h[v]) < G.n) {
-            if (__ldg(&G.row[v + 1]) - __ldg(&G.row[v]) <= kHubDeg)
-                add = atomicExch(&G.astamp[v], AL.stamp) != AL.stamp;
+__device__ __forceinline__ void note_activation_n(const DevGraph &G, const int (&d)[kIlp], const int (&v)[kIlp],
+                                                  const long long (&old)[kIlp], const ActList &AL) {
+    bool cand[kIlp];
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        const bool turned = PULL ? (old[j] >= 0 && old[j] - d[j] < 0) : (old[j] <= 0 && old[j] + d[j] > 0);
+        cand[j] = d[j] > 0 && turned && v[j] != G.s && v[j] != G.t;
+        any |= cand[j];
+    }
+    if (!__any_sync(kFull, any)) return;
+    int hv[kIlp], deg[kIlp];
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        hv[j] = cand[j] ? lcg(&G.h[v[j]]) : G.n;
+        deg[j] = cand[j] ? __ldg(&G.row[v[j] + 1]) - __ldg(&G.row[v[j]]) : 0;
+    }
+    bool add[kIlp], add_hub[kIlp];
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        add[j] = add_hub[j] = false;
+        if (hv[j] < G.n) {
+            if (deg[j] <= kHubDeg)
+                add[j] = atomicExch(&G.astamp[v[j]], AL.stamp) != AL.stamp;
             else
-                add_hub = atomicExch(&G.astamp[v], AL.hstamp) != AL.hstamp;
+                add_hub[j] = atomicExch(&G.astamp[v[j]], AL.hstamp) != AL.hstamp;
         }
     }
-    warp_append(add, v, AL.cnt, AL.list);
-    warp_append(add_hub, v, AL.hcnt, AL.hlist);
-}
-
-__device__ __forceinline__ void note_activation(const DevGraph &G, bool pushed, int v, long long old, long long d,
-                                                const ActList &AL) {
-    note_activation_t<false>(G, pushed, v, old, d, AL);
+    warp_append_n(add, v, AL.cnt, AL.list);
+    warp_append_n(add_hub, v, AL.hcnt, AL.hlist);
 }
 
 // One round of a warp's arc scan: lane i holds arcs a0 + 32 j + i (j < kIlp)
@@ -779,23 +863,27 @@ __device__ __forceinline__ void push_relabel_small_t(const DevGraph &G, int u, i
             __syncwarp();
             continue;
         }
-        long long rem = eu, sent = 0;
+        long long rem = eu, sent = 0, old[kIlp];
+        int d[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             const int ra = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
             const long long incl = warp_incl_scan(ra);
-            long long d = rem - (incl - ra);
-            d = d < 0 ? 0 : (d > ra ? ra : d);
-            long long old = 0;
-            if (d > 0) {
-                old = move_arc<PULL>(G, beg + 32 * j + lane, R.v[j], (int)d);
-                sent += d;
-                ++K.push;
-            }
-            note_activation_t<PULL>(G, d > 0, R.v[j], old, d, AL);
+            const long long dj = rem - (incl - ra);
+            d[j] = dj < 0 ? 0 : (dj > ra ? ra : (int)dj);
             const long long tot = __shfl_sync(kFull, incl, 31);
             rem -= tot < rem ? tot : rem;
         }
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            old[j] = 0;
+            if (d[j] > 0) {
+                old[j] = move_arc<PULL>(G, beg + 32 * j + lane, R.v[j], d[j]);
+                sent += d[j];
+                ++K.push;
+            }
+        }
+        note_activation_n<PULL>(G, d, R.v, old, AL);
         sent = warp_sum(sent);
         if (lane == 0 && sent) add_ll(&G.e[u], PULL ? sent : -sent);
         __syncwarp();
@@ -856,22 +944,27 @@ __device__ __forceinline__ void push_relabel_warp_t(const DevGraph &G, int u, in
             ArcRound R;
             load_round_t<PULL>(G, a0, end, R, pt, side);
             K.pr_arcs += round_arcs(a0, end);
+            long long old[kIlp];
+            int d[kIlp];
 #pragma unroll
             for (int j = 0; j < kIlp; ++j) {
                 const int ra = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
                 const long long incl = warp_incl_scan(ra);
-                long long d = rem - (incl - ra);
-                d = d < 0 ? 0 : (d > ra ? ra : d);
-                long long old = 0;
-                if (d > 0) {
-                    old = move_arc<PULL>(G, a0 + 32 * j + lane, R.v[j], (int)d);
-                    sent += d;
-                    ++K.push;
-                }
-                note_activation_t<PULL>(G, d > 0, R.v[j], old, d, AL);
+                const long long dj = rem - (incl - ra);
+                d[j] = dj < 0 ? 0 : (dj > ra ? ra : (int)dj);
                 const long long tot = __shfl_sync(kFull, incl, 31);
                 rem -= tot < rem ? tot : rem;
             }
+#pragma unroll
+            for (int j = 0; j < kIlp; ++j) {
+                old[j] = 0;
+                if (d[j] > 0) {
+                    old[j] = move_arc<PULL>(G, a0 + 32 * j + lane, R.v[j], d[j]);
+                    sent += d[j];
+                    ++K.push;
+                }
+            }
+            note_activation_n<PULL>(G, d, R.v, old, AL);
         }
         sent = warp_sum(sent);
         if (lane == 0 && sent) add_ll(&G.e[u], PULL ? sent : -sent);
@@ -978,18 +1071,20 @@ __device__ __forceinline__ long long hub_move_item(const DevGraph &G, int a0, in
             old = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(rem), (unsigned long long)(-tot));
         old = __shfl_sync(kFull, old, 0);
         if (old <= 0) break;
+        long long prev[kIlp];
+        int d[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
-            long long d = old - (incl[j] - ra[j]);
-            d = d < 0 ? 0 : (d > ra[j] ? ra[j] : d);
-            long long prev = 0;
-            if (d > 0) {
-                prev = move_arc<PULL>(G, a0 + 32 * j + lane, R.v[j], (int)d);
-                sent += d;
+            const long long dj = old - (incl[j] - ra[j]);
+            d[j] = dj < 0 ? 0 : (dj > ra[j] ? ra[j] : (int)dj);
+            prev[j] = 0;
+            if (d[j] > 0) {
+                prev[j] = move_arc<PULL>(G, a0 + 32 * j + lane, R.v[j], d[j]);
+                sent += d[j];
                 ++K.push;
             }
-            note_activation_t<PULL>(G, d > 0, R.v[j], prev, d, AL);
         }
+        note_activation_n<PULL>(G, d, R.v, prev, AL);
     }
     return warp_sum(sent);
 }
@@ -1047,6 +1142,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     const int nwarps = (int)(gthreads >> 5);
     const int n = G.n, s = G.s, t = G.t;
     Counters K;
+    // BFS frontiers in shared memory: CTA 0's small-frontier levels, and the
+    // warps' staged entries in grid-wide levels (barriers keep them apart)
+    __shared__ __align__(16) int s_bfs[2 * kSoloCap];
+    static_assert(kWq * (kBlock / 32) <= 2 * kSoloCap, "frontier stages exceed the shared frontier");
+    static_assert(kWq >= 32 * kIlp, "a stage holds one round of arcs");
     unsigned long long tprev = gtimer();
     long long it = -1;   // loop iteration (-1 before the loop, for trace records)
 
@@ -1328,7 +1428,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 // level's counters before CTA 0 starts (the first barrier).
                 MF_SYNC_T(S_T_BFS, L, 6, cur);
                 if (blockIdx.x == 0) {
-                    __shared__ int s_front[2][kSoloCap];
+                    int (*s_front)[kSoloCap] = reinterpret_cast<int (*)[kSoloCap]>(s_bfs);
                     __shared__ int s_cnt[2];
                     __shared__ long long s_arcs[2];
                     __shared__ int s_big;
@@ -1346,11 +1446,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     for (;;) {
                         int *ccs = &C->ccnt[Ls % 3];
                         int *spill = (Ls & 1) ? G.qb0 : G.qb1;   // positions >= kSoloCap of the next frontier
-                        for (int grp = cw; grp * 32 < cs; grp += kBlock / 32) {
-                            const int idx = grp * 32 + lane;
+                        Front SF{&s_cnt[b ^ 1], s_front[b ^ 1], &s_arcs[b ^ 1], kSoloCap, spill, nullptr, 0, 0};
+                        int gs = 32;   // frontier vertices per warp: fewer when they do not fill the warps
+                        while (gs > 1 && (gs >> 1) * (kBlock / 32) >= cs) gs >>= 1;
+                        for (int grp = cw; grp * gs < cs; grp += kBlock / 32) {
+                            const int idx = grp * gs + lane;
                             int beg = 0, deg = 0;
                             bool fwd = false;
-                            if (idx < cs) {
+                            if (lane < gs && idx < cs) {
                                 const int u = s_front[b][idx];
                                 fwd = dual && G.part[u] == kPartS;
                                 beg = __ldg(&G.row[u]);
@@ -1363,8 +1466,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                                     deg = 0;
                                 }
                             }
-                            bfs_expand_warp(G, beg, deg, fwd, dual, Ls, &s_cnt[b ^ 1], s_front[b ^ 1],
-                                            &s_arcs[b ^ 1], K, kSoloCap, spill);
+                            bfs_expand_warp(G, beg, deg, fwd, dual, Ls, SF, K);
                         }
                         __syncthreads();
                         if (s_big) {
@@ -1381,8 +1483,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                                         a[j] = ab + 32 * j + lane;
                                         ok[j] = a[j] < a1;
                                     }
-                                    bfs_visit_n(G, a, ok, fw, dual, Ls, &s_cnt[b ^ 1], s_front[b ^ 1],
-                                                &s_arcs[b ^ 1], K, kSoloCap, spill);
+                                    bfs_visit_n(G, a, ok, fw, dual, Ls, SF, K);
                                 }
                             }
                             __syncthreads();
@@ -1437,18 +1538,23 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 C->asum[(L + 2) % 3] = 0;
                 if (bottom_up) ST[S_BU_LEVELS] += 1;
             }
+            Front FR{ncnt, NF, asum, 0x7fffffff, nullptr, s_bfs + (threadIdx.x >> 5) * kWq, 0, 0};
             if (bottom_up) {
                 // groups of 32 consecutive vertex ids (warp w first, then tickets)
                 const int groups = (n + 31) / 32;
                 for (int grp = gwarp; grp < groups; grp = next_ticket(&C->gtk[L % 3], nwarps))
-                    bfs_bottom_up_group(G, grp * 32, dual, L, ncnt, NF, asum, ccnt, K);
+                    bfs_bottom_up_group(G, grp * 32, dual, L, FR, ccnt, K);
             } else {
-                // groups of 32 frontier vertices (warp w first, then tickets)
-                for (int grp = gwarp; grp * 32 < cur; grp = next_ticket(&C->gtk[L % 3], nwarps)) {
-                    const int idx = grp * 32 + lane;
+                // groups of gs frontier vertices (warp w first, then tickets):
+                // 32, or fewer when the frontier does not fill the grid's warps,
+                // so that the arcs of a small frontier still spread over them
+                int gs = 32;
+                while (gs > 1 && (long long)(gs >> 1) * nwarps >= cur) gs >>= 1;
+                for (int grp = gwarp; grp * gs < cur; grp = next_ticket(&C->gtk[L % 3], nwarps)) {
+                    const int idx = grp * gs + lane;
                     int beg = 0, deg = 0;
                     bool fwd = false;
-                    if (idx < cur) {
+                    if (lane < gs && idx < cur) {
                         const int u = lcg(&F[idx]);
                         fwd = dual && G.part[u] == kPartS;
                         beg = __ldg(&G.row[u]);
@@ -1460,16 +1566,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             deg = 0;
                         }
                     }
-                    bfs_expand_warp(G, beg, deg, fwd, dual, L, ncnt, NF, asum, K);
+                    bfs_expand_warp(G, beg, deg, fwd, dual, L, FR, K);
                 }
             }
+            front_flush(FR);
             MF_SYNC_T(S_T_BFS, L, bottom_up ? 2 : 0, cur);
             const int nch = lcg(ccnt);
             if (nch > 0) {
                 for (int c = gwarp; c < nch; c = next_ticket(&C->ctk[L % 3], nwarps)) {
                     const int2 item = lcg(&G.cb[c]);
                     if (bottom_up) {
-                        bfs_bottom_up_item(G, item, dual, L, ncnt, NF, asum, K);
+                        bfs_bottom_up_item(G, item, dual, L, FR, K);
                         continue;
                     }
                     const unsigned fw = (dual && G.part[item.x] == kPartS) ? (1u << kIlp) - 1u : 0u;
@@ -1482,9 +1589,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             a[j] = ab + 32 * j + lane;
                             ok[j] = a[j] < a1;
                         }
-                        bfs_visit_n(G, a, ok, fw, dual, L, ncnt, NF, asum, K);
+                        bfs_visit_n(G, a, ok, fw, dual, L, FR, K);
                     }
                 }
+                front_flush(FR);
                 MF_SYNC_T(S_T_BFS, L, bottom_up ? 3 : 1, nch);
             }
             ++L;
