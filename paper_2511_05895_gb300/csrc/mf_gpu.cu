@@ -71,13 +71,18 @@ enum ExitKind { EXIT_BFS = 0, EXIT_CLEAN = 1, EXIT_NO_CUT_CHANGE = 2, EXIT_PUSH_
 constexpr int kMaxRounds = 16;
 constexpr int kMinHubCycles = 4;
 // PushRelabel passes per loop iteration (hub cycles, then activation rounds;
-// a pass that turns hubs active again hands them to the next pass)
+// a pass that turns hubs active again hands them to the next pass, when
+// there are at most kPassHubs of them).  The push-pull instance takes more:
+// there the re-activated hubs are few and another pass costs much less than
+// another dual BFS (measured on RMAT-20: 1.66 -> 1.32 ms per repair).
 constexpr int kMaxPasses = 2;
+constexpr int kMaxPassesPP = 4;
 // BFS levels whose frontier has at most this many arcs and vertices run on
 // CTA 0 alone, with the frontiers in shared memory
 constexpr long long kSoloArcs = 8192;
 constexpr int kSoloCap = 4096;
 constexpr int kPassHubs = 32;   // most re-activated hubs a further pass takes
+constexpr int kPassHubsPP = 64;
 
 constexpr int S_COUNT_MAX = 24;
 
@@ -315,23 +320,25 @@ struct Counters {
               ri_moves = 0, clamped = 0, resat = 0;
 };
 
-constexpr int kIlp = 4;   // arcs in flight per lane in the BFS
+constexpr int kIlp = 4;    // arcs in flight per lane in PushRelabel and RemoveInvalidEdges
+constexpr int kIlpB = 4;   // arcs in flight per lane in the BFS
 
 struct ArcRoundBfs {
-    int ra[kIlp], w[kIlp];
+    int ra[kIlpB], w[kIlpB];
 };
 
-// Warp-aggregated append of the lanes' flagged values of kIlp slots: one
+// Warp-aggregated append of the lanes' flagged values of N slots: one
 // atomicAdd for the whole warp and all slots; positions from cap on go to
 // spill (same positions) instead of buf.  All 32 lanes call.
-__device__ __forceinline__ void warp_append_n(const bool (&pred)[kIlp], const int (&val)[kIlp], int *cnt, int *buf,
+template <int N>
+__device__ __forceinline__ void warp_append_n(const bool (&pred)[N], const int (&val)[N], int *cnt, int *buf,
                                               int cap = 0x7fffffff, int *spill = nullptr) {
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
-    unsigned m[kIlp];
+    unsigned m[N];
     int tot = 0;
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
+    for (int j = 0; j < N; ++j) {
         m[j] = __ballot_sync(kFull, pred[j]);
         tot += __popc(m[j]);
     }
@@ -340,7 +347,7 @@ __device__ __forceinline__ void warp_append_n(const bool (&pred)[kIlp], const in
     if (lane == 0) base = atomicAdd(cnt, tot);
     base = __shfl_sync(kFull, base, 0);
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
+    for (int j = 0; j < N; ++j) {
         if (pred[j]) {
             const int pos = base + __popc(m[j] & below);
             (pos < cap ? buf : spill)[pos] = val[j];
@@ -387,18 +394,19 @@ __device__ __forceinline__ void front_flush(Front &F) {
     F.ds = 0;
 }
 
-// Append the lanes' flagged values of kIlp slots (at most 32 kIlp <= kWq
+// Append the lanes' flagged values of N slots (at most 32 N <= kWq
 // entries).  All 32 lanes call.
-__device__ __forceinline__ void front_append_n(const bool (&pred)[kIlp], const int (&val)[kIlp], Front &F) {
+template <int N>
+__device__ __forceinline__ void front_append_n(const bool (&pred)[N], const int (&val)[N], Front &F) {
     if (!F.stage) {
         warp_append_n(pred, val, F.cnt, F.buf, F.cap, F.spill);
         return;
     }
     const unsigned below = (1u << (threadIdx.x & 31)) - 1u;
-    unsigned m[kIlp];
+    unsigned m[N];
     int tot = 0;
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
+    for (int j = 0; j < N; ++j) {
         m[j] = __ballot_sync(kFull, pred[j]);
         tot += __popc(m[j]);
     }
@@ -406,7 +414,7 @@ __device__ __forceinline__ void front_append_n(const bool (&pred)[kIlp], const i
     if (F.sn + tot > kWq) front_flush_entries(F);
     int base = F.sn;
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
+    for (int j = 0; j < N; ++j) {
         if (pred[j]) F.stage[base + __popc(m[j] & below)] = val[j];
         base += __popc(m[j]);
     }
@@ -418,26 +426,26 @@ __device__ __forceinline__ void front_add_arcs(Front &F, long long ds) {
     else if ((threadIdx.x & 31) == 0 && ds) add_ll(F.asum, ds);
 }
 
-// bfs_discovered for kIlp slots per lane at once: the loads of all slots are
+// bfs_discovered for kIlpB slots per lane at once: the loads of all slots are
 // issued together and each list gets one reservation per warp.
-__device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (&disc)[kIlp], const int (&v)[kIlp],
+__device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (&disc)[kIlpB], const int (&v)[kIlpB],
                                                  unsigned fwd, bool dual, Front &F, Counters &K) {
     bool any = false;
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) any |= disc[j];
+    for (int j = 0; j < kIlpB; ++j) any |= disc[j];
     if (!__any_sync(kFull, any)) return;
     front_append_n(disc, v, F);
-    int deg[kIlp];
-    long long ev[kIlp];
+    int deg[kIlpB];
+    long long ev[kIlpB];
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
+    for (int j = 0; j < kIlpB; ++j) {
         deg[j] = disc[j] ? __ldg(&G.row[v[j] + 1]) - __ldg(&G.row[v[j]]) : 0;
         ev[j] = disc[j] ? lcg(&G.e[v[j]]) : 0;
     }
     long long ds = 0;
-    bool small[kIlp], hub[kIlp];
+    bool small[kIlpB], hub[kIlpB];
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
+    for (int j = 0; j < kIlpB; ++j) {
         ds += deg[j];
         K.bfs_verts += disc[j];
         // a vertex of the pull side (forward search) is active when deficient
@@ -458,10 +466,8 @@ __device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int
                                                Front &F, Counters &K) {
     if (!__ballot_sync(kFull, disc)) return;
     {
-        bool p[kIlp] = {};
-        int x[kIlp] = {};
-        p[0] = disc;
-        x[0] = v;
+        const bool p[1] = {disc};
+        const int x[1] = {v};
         front_append_n(p, x, F);
     }
     int deg = 0;
@@ -480,7 +486,7 @@ __device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int
     }
 }
 
-// Backward BFS step over kIlp arcs per lane (a[j] of frontier vertex u, head
+// Backward BFS step over kIlpB arcs per lane (a[j] of frontier vertex u, head
 // v; ok[j] marks a real arc): the arc v -> u is residual iff rr[a] > 0; an
 // unvisited v (height n) gets height L + 1 (global relabel, Sec. 2.2).  Newly
 // reached vertices with positive excess are active and join the worklist
@@ -488,21 +494,21 @@ __device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int
 // to the pull side of a push-pull repair and search forward instead: u -> v
 // residual (r[a] > 0), and a deficient v is active.  Every load of a round is
 // issued before any of them is used.  All 32 lanes call.
-__device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kIlp], const bool (&ok)[kIlp],
+__device__ __forceinline__ void bfs_visit_n(const DevGraph &G, const int (&a)[kIlpB], const bool (&ok)[kIlpB],
                                             unsigned fwd, bool dual, int L, Front &F, Counters &K) {
     const int n = G.n;
-    int v[kIlp], rin[kIlp], hv[kIlp];
-    bool disc[kIlp];
+    int v[kIlpB], rin[kIlpB], hv[kIlpB];
+    bool disc[kIlpB];
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
+    for (int j = 0; j < kIlpB; ++j) {
         v[j] = ok[j] ? __ldg(&G.head[a[j]]) : 0;
         rin[j] = ok[j] ? lcg(((fwd >> j) & 1u) ? &G.r[a[j]] : &G.rr[a[j]]) : 0;
         K.bfs_arcs += ok[j];
     }
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) hv[j] = (rin[j] > 0 && v[j] != G.s) ? lcg(&G.h[v[j]]) : -1;
+    for (int j = 0; j < kIlpB; ++j) hv[j] = (rin[j] > 0 && v[j] != G.s) ? lcg(&G.h[v[j]]) : -1;
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) disc[j] = hv[j] == n && atomicCAS(&G.h[v[j]], n, L + 1) == n;
+    for (int j = 0; j < kIlpB; ++j) disc[j] = hv[j] == n && atomicCAS(&G.h[v[j]], n, L + 1) == n;
     bfs_discovered_n(G, disc, v, fwd, dual, F, K);
 }
 
@@ -522,12 +528,12 @@ __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int 
     }
     const int total = __shfl_sync(kFull, incl, 31);
     const int excl = incl - deg;
-    for (int k0 = 0; k0 < total; k0 += 32 * kIlp) {
-        int a[kIlp];
-        bool ok[kIlp];
+    for (int k0 = 0; k0 < total; k0 += 32 * kIlpB) {
+        int a[kIlpB];
+        bool ok[kIlpB];
         unsigned fw = 0;
 #pragma unroll
-        for (int jj = 0; jj < kIlp; ++jj) {
+        for (int jj = 0; jj < kIlpB; ++jj) {
             const int k = k0 + 32 * jj + lane;
             int j = 0;  // owner lane: largest j with excl_j <= k
 #pragma unroll
@@ -584,10 +590,10 @@ __device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base,
         const int total = __shfl_sync(kFull, incl, 31);
         const int excl = incl - deg;
         const unsigned pull_lanes = __ballot_sync(kFull, side == kPartS);
-        for (int k0 = 0; k0 < total && found != want; k0 += 32 * kIlp) {
-            int a[kIlp], own[kIlp], ra[kIlp], w[kIlp];
+        for (int k0 = 0; k0 < total && found != want; k0 += 32 * kIlpB) {
+            int a[kIlpB], own[kIlpB], ra[kIlpB], w[kIlpB];
 #pragma unroll
-            for (int jj = 0; jj < kIlp; ++jj) {
+            for (int jj = 0; jj < kIlpB; ++jj) {
                 const int k = k0 + 32 * jj + lane;
                 int j = 0;
 #pragma unroll
@@ -605,7 +611,7 @@ __device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base,
             }
             unsigned hit = 0;
 #pragma unroll
-            for (int jj = 0; jj < kIlp; ++jj)
+            for (int jj = 0; jj < kIlpB; ++jj)
                 if (ra[jj] > 0 && lcg(&G.h[w[jj]]) == L &&
                     (!dual || G.part[w[jj]] == (((pull_lanes >> own[jj]) & 1u) ? kPartS : kPartT)))
                     hit |= 1u << own[jj];
@@ -628,11 +634,11 @@ __device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item,
     if (lcg(&G.h[v]) == G.n) {
         const int a1 = min(item.y + kChunk, __ldg(&G.row[v + 1]));
         bool hit = false;
-        for (int a0 = item.y; a0 < a1 && !hit; a0 += 32 * kIlp) {
+        for (int a0 = item.y; a0 < a1 && !hit; a0 += 32 * kIlpB) {
             if (a0 != item.y && __shfl_sync(kFull, lane == 0 ? lcg(&G.h[v]) : 0, 0) != G.n) break;
             ArcRoundBfs R;
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j) {
+            for (int j = 0; j < kIlpB; ++j) {
                 const int a = a0 + 32 * j + lane;
                 R.ra[j] = a < a1 ? lcg(side == kPartS ? &G.rr[a] : &G.r[a]) : 0;
                 R.w[j] = a < a1 ? __ldg(&G.head[a]) : 0;
@@ -640,7 +646,7 @@ __device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item,
             }
             bool mine = false;
 #pragma unroll
-            for (int j = 0; j < kIlp; ++j)
+            for (int j = 0; j < kIlpB; ++j)
                 mine |= R.ra[j] > 0 && lcg(&G.h[R.w[j]]) == L && (!dual || G.part[R.w[j]] == side);
             hit = __any_sync(kFull, mine);
         }
@@ -1146,7 +1152,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     // warps' staged entries in grid-wide levels (barriers keep them apart)
     __shared__ __align__(16) int s_bfs[2 * kSoloCap];
     static_assert(kWq * (kBlock / 32) <= 2 * kSoloCap, "frontier stages exceed the shared frontier");
-    static_assert(kWq >= 32 * kIlp, "a stage holds one round of arcs");
+    static_assert(kWq >= 32 * kIlpB, "a stage holds one round of arcs");
     unsigned long long tprev = gtimer();
     long long it = -1;   // loop iteration (-1 before the loop, for trace records)
 
@@ -1473,13 +1479,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             const int nch = lcg(ccs);
                             for (int c = cw; c < nch; c += kBlock / 32) {
                                 const int2 item = lcg(&G.cb[c]);
-                                const unsigned fw = (dual && G.part[item.x] == kPartS) ? (1u << kIlp) - 1u : 0u;
+                                const unsigned fw = (dual && G.part[item.x] == kPartS) ? (1u << kIlpB) - 1u : 0u;
                                 const int a1 = min(item.y + kChunk, __ldg(&G.row[item.x + 1]));
-                                for (int ab = item.y; ab < a1; ab += 32 * kIlp) {
-                                    int a[kIlp];
-                                    bool ok[kIlp];
+                                for (int ab = item.y; ab < a1; ab += 32 * kIlpB) {
+                                    int a[kIlpB];
+                                    bool ok[kIlpB];
 #pragma unroll
-                                    for (int j = 0; j < kIlp; ++j) {
+                                    for (int j = 0; j < kIlpB; ++j) {
                                         a[j] = ab + 32 * j + lane;
                                         ok[j] = a[j] < a1;
                                     }
@@ -1579,13 +1585,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         bfs_bottom_up_item(G, item, dual, L, FR, K);
                         continue;
                     }
-                    const unsigned fw = (dual && G.part[item.x] == kPartS) ? (1u << kIlp) - 1u : 0u;
+                    const unsigned fw = (dual && G.part[item.x] == kPartS) ? (1u << kIlpB) - 1u : 0u;
                     const int a1 = min(item.y + kChunk, __ldg(&G.row[item.x + 1]));
-                    for (int ab = item.y; ab < a1; ab += 32 * kIlp) {
-                        int a[kIlp];
-                        bool ok[kIlp];
+                    for (int ab = item.y; ab < a1; ab += 32 * kIlpB) {
+                        int a[kIlpB];
+                        bool ok[kIlpB];
 #pragma unroll
-                        for (int j = 0; j < kIlp; ++j) {
+                        for (int j = 0; j < kIlpB; ++j) {
                             a[j] = ab + 32 * j + lane;
                             ok[j] = a[j] < a1;
                         }
@@ -1646,7 +1652,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         // (grids) finishing a few active vertices by rounds is cheaper than
         // another global relabel.
         const int max_rounds = L > kMaxRounds ? L : kMaxRounds;
-        for (int pass = 0; pass < kMaxPasses; ++pass) {
+        for (int pass = 0; pass < (PP ? kMaxPassesPP : kMaxPasses); ++pass) {
             const int *HL = (pass & 1) ? G.hl2 : G.hl;
             const int nhp = pass == 0 ? nh : pend;
             const unsigned wstamp = snext++;   // this pass's round-0 list
@@ -1918,7 +1924,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             pend = lcg(pcnt);   // every append to it came before the pass's last barrier
             // another pass only for a few re-activated hubs: a large set of
             // them is better served after a global relabel
-            if (pend == 0 || pend > kPassHubs || !pass_hubs_clean || !pass_rounds_clean) break;
+            if (pend == 0 || pend > (PP ? kPassHubsPP : kPassHubs) || !pass_hubs_clean || !pass_rounds_clean)
+                break;
         }
 
         // RemoveInvalidEdges (Alg. 3): relabelled vertices by warps,
@@ -2191,7 +2198,7 @@ struct NoAllocLayout {
     static constexpr size_t total = hri + align256(sizeof(int2) * (kNoAllocMaxArcs / kPrChunk + kNoAllocMaxHubs));
 };
 
-static_assert(NoAllocLayout::total == 13533952, "the header states the scratch size (13,533,952 bytes)");
+static_assert(NoAllocLayout::total == 13239040, "the header states the scratch size (13,239,040 bytes)");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NoAllocLayout::total];
 
 }  // namespace mf

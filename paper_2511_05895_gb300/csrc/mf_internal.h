@@ -17,7 +17,7 @@ constexpr int kChunk = 256;
 // RemoveInvalidEdges cooperatively over the whole grid, in kPrChunk-arc work
 // items; smaller ones are handled by one warp each.
 constexpr int kHubDeg = 512;
-constexpr int kPrChunk = 128;
+constexpr int kPrChunk = 256;
 
 // Host image of the Bi-CSR of Sec. 5.1.  Vertex u owns arcs row[u] ..
 // row[u+1]-1, one per distinct neighbour v (u -> v edge, v -> u edge, or
