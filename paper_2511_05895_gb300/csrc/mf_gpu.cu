@@ -97,12 +97,9 @@ struct Ctl {
     unsigned bar_pad;
     int qcnt[3];          // (z) BFS frontier sizes, rotating by level
     int ccnt[3];          // (z) BFS chunk-item counts, rotating by level
-    int gtk[3];           // (z) BFS frontier-group tickets, rotating by level
-    int ctk[3];           // (z) BFS chunk-item tickets, rotating by level
     long long asum[3];    // (z) sum of the degrees of each BFS frontier, rotating
     int acnt[3];          // (z) activation-round list sizes, rotating by round
     int rlcnt;            // (z) relabel list size
-    int rtk[3];           // (z) activation-round tickets, rotating by round
     unsigned stamp_base;  // first activation stamp of the next launch (kept across launches)
     unsigned bseq;        // sequence number of the last batch (duplicate-id stamps)
     int wcnt;             // (z) active worklist size (vertices of degree <= kHubDeg)
@@ -201,16 +198,6 @@ struct Job {
 __device__ __forceinline__ int lcg(const int *p) { return __ldcg(p); }
 __device__ __forceinline__ long long lcg(const long long *p) { return __ldcg(p); }
 __device__ __forceinline__ int2 lcg(const int2 *p) { return __ldcg(p); }
-
-// Work items of a phase over the grid's warps: warp w starts with item w and
-// then takes tickets, offset by the warp count, so a phase with fewer items
-// than warps runs without any atomic and a large one stays balanced.  All 32
-// lanes call; returns the warp's next item.
-__device__ __forceinline__ int next_ticket(int *ticket, int nwarps) {
-    int t = 0;
-    if ((threadIdx.x & 31) == 0) t = atomicAdd(ticket, 1);
-    return __shfl_sync(0xffffffffu, t, 0) + nwarps;
-}
 
 __device__ __forceinline__ void add_ll(long long *p, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
@@ -1356,10 +1343,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             C->qcnt[1] = 0;
             C->qcnt[2] = 0;
             C->ccnt[0] = 0;
-            C->gtk[0] = C->ctk[0] = 0;
             C->asum[1] = C->asum[2] = 0;
             C->acnt[0] = C->acnt[1] = C->acnt[2] = 0;
-            C->rtk[0] = C->rtk[1] = C->rtk[2] = 0;
             C->rlcnt = 0;
             C->rhcnt = 0;
             C->phc[1] = 0;
@@ -1520,8 +1505,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         C->asum[Ls % 3] = mfs;
                         C->qcnt[(Ls + 1) % 3] = 0;
                         C->asum[(Ls + 1) % 3] = 0;
-                        C->gtk[Ls % 3] = 0;
-                        C->ctk[Ls % 3] = 0;
                         C->solo_L = Ls;
                         C->solo_seen = seen;   // arcs of the levels run, without level Ls
                     }
@@ -1539,24 +1522,22 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             if (gtid == 0) {
                 C->qcnt[(L + 2) % 3] = 0;
                 C->ccnt[(L + 1) % 3] = 0;
-                C->gtk[(L + 1) % 3] = 0;
-                C->ctk[(L + 1) % 3] = 0;
                 C->asum[(L + 2) % 3] = 0;
                 if (bottom_up) ST[S_BU_LEVELS] += 1;
             }
             Front FR{ncnt, NF, asum, 0x7fffffff, nullptr, s_bfs + (threadIdx.x >> 5) * kWq, 0, 0};
             if (bottom_up) {
-                // groups of 32 consecutive vertex ids (warp w first, then tickets)
+                // groups of 32 consecutive vertex ids (warp w: groups w, w + W, ...)
                 const int groups = (n + 31) / 32;
-                for (int grp = gwarp; grp < groups; grp = next_ticket(&C->gtk[L % 3], nwarps))
+                for (int grp = gwarp; grp < groups; grp += nwarps)
                     bfs_bottom_up_group(G, grp * 32, dual, L, FR, ccnt, K);
             } else {
-                // groups of gs frontier vertices (warp w first, then tickets):
+                // groups of gs frontier vertices (warp w: groups w, w + W, ...):
                 // 32, or fewer when the frontier does not fill the grid's warps,
                 // so that the arcs of a small frontier still spread over them
                 int gs = 32;
                 while (gs > 1 && (long long)(gs >> 1) * nwarps >= cur) gs >>= 1;
-                for (int grp = gwarp; grp * gs < cur; grp = next_ticket(&C->gtk[L % 3], nwarps)) {
+                for (int grp = gwarp; grp * gs < cur; grp += nwarps) {
                     const int idx = grp * gs + lane;
                     int beg = 0, deg = 0;
                     bool fwd = false;
@@ -1579,7 +1560,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             MF_SYNC_T(S_T_BFS, L, bottom_up ? 2 : 0, cur);
             const int nch = lcg(ccnt);
             if (nch > 0) {
-                for (int c = gwarp; c < nch; c = next_ticket(&C->ctk[L % 3], nwarps)) {
+                for (int c = gwarp; c < nch; c += nwarps) {
                     const int2 item = lcg(&G.cb[c]);
                     if (bottom_up) {
                         bfs_bottom_up_item(G, item, dual, L, FR, K);
@@ -1667,7 +1648,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     *pcnt = 0;
                     C->wcnt = 0;
                     C->acnt[0] = C->acnt[1] = C->acnt[2] = 0;
-                    C->rtk[0] = C->rtk[1] = C->rtk[2] = 0;
                 }
                 C->hub_act[0] = C->hub_act[1] = 0;
                 C->hlc[0] = C->hlc[1] = 0;
@@ -1877,14 +1857,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     const ActList AL{&C->acnt[(rd + 1) % 3], nlist, snext++, rstamp_it, pcnt, AL0.hlist, hstamp};
                     if (gtid == 0) {
                         C->acnt[(rd + 2) % 3] = 0;
-                        C->rtk[(rd + 1) % 3] = 0;
                         ST[S_ROUNDS] += 1;
                         ST[S_WL] += cnt;
                     }
                     if (rd == 0 && pass == 0 && J.mode == MF_MODE_TOPOLOGY) {
                         // topology-driven (Sec. 5.2): every vertex id is visited;
                         // each warp takes 32 ids and serves the active ones
-                        for (int grp = gwarp; grp * 32 < n; grp = next_ticket(&C->rtk[0], nwarps)) {
+                        for (int grp = gwarp; grp * 32 < n; grp += nwarps) {
                             const int base = grp * 32;
                             const int v = base + lane;
                             bool act = false;
@@ -1900,7 +1879,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     } else if (stage == 1) {
                         // push-pull: push on T (h+), pull on S (h-), each side
                         // only over arcs within it
-                        for (int i = gwarp; i < cnt; i = next_ticket(&C->rtk[rd % 3], nwarps)) {
+                        for (int i = gwarp; i < cnt; i += nwarps) {
                             const int u = lcg(&list[i]);
                             const unsigned char side = G.part[u];
                             if (side == kPartS)
@@ -1909,7 +1888,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                                 push_relabel_warp_t<false>(G, u, kc, AL, G.part, side, K);
                         }
                     } else {
-                        for (int i = gwarp; i < cnt; i = next_ticket(&C->rtk[rd % 3], nwarps))
+                        for (int i = gwarp; i < cnt; i += nwarps)
                             push_relabel_warp(G, lcg(&list[i]), kc, AL, K);
                     }
                     MF_SYNC_T(S_T_PRW, rd, 0, cnt);
@@ -2021,12 +2000,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         C->rhcnt = 0;
         C->inc_block = 0;
         for (int i = 0; i < 3; ++i) {
-            C->qcnt[i] = C->ccnt[i] = C->gtk[i] = C->ctk[i] = 0;
+            C->qcnt[i] = C->ccnt[i] = 0;
             C->asum[i] = 0;
         }
         C->wcnt = C->hcnt = C->hccnt = C->rlcnt = 0;
         C->acnt[0] = C->acnt[1] = C->acnt[2] = 0;
-        C->rtk[0] = C->rtk[1] = C->rtk[2] = 0;
         C->stamp_base = snext;
         if (batch_job) C->bseq = seq;
         C->hub_act[0] = C->hub_act[1] = 0;
