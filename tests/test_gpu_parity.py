@@ -95,6 +95,25 @@ def test_small_launch_shapes(mf, grid_blocks):
     G.close()
 
 
+@pytest.mark.parametrize("mode", ["data-driven", "push-pull"])
+@pytest.mark.parametrize("grid_blocks", [1, 3])
+def test_few_ctas_on_a_power_law_graph(mf, mode, grid_blocks):
+    """RMAT-15 on 1 or 3 CTAs: every warp serves a thousand vertices or more
+    per BFS level, so its staged frontier fills and is published in the middle
+    of a level many times (bottom-up and top-down), and every fixed-stride
+    loop of a phase wraps around the warps many times."""
+    g = gen.rmat(scale=15, seed=91)
+    opts = {"grid_blocks": grid_blocks}
+    if mode == "push-pull":
+        opts["mode"] = mf.MF_MODE_PUSH_PULL
+
+    def batches(cap):
+        yield gen.mixed_batch(cap, g.m // 1000, 1, 500, seed=91, index=0)
+        yield gen.mixed_batch(cap, g.m // 100, 1, 500, seed=91, index=1)
+    G, _ = run_batches(mf, g, batches, **opts)
+    G.close()
+
+
 @pytest.mark.parametrize("kc", [1, 2, 64])
 def test_kernel_cycles_do_not_change_the_value(mf, kc):
     g = gen.random_graph(seed=100 + kc)
