@@ -115,6 +115,9 @@ struct Ctl {
     int pol_kc;
     int pol_fallback;     // 1 if the learned policy fell back to the plain rule
     float feat[12];       // features of the last batch the policy kernel saw
+    long long pol_acc[3]; // (z) k_policy's batch sums: increments, entries at s or t, sum |delta|
+    int pol_done;         // (z) k_policy CTAs that have added their sums
+    int pad3;
     int abort_loop;       // (z) set by thread 0 when the wall-clock limit passed
     int trace_n;          // trace records written by the current launch
     int ri_moved[2];      // (z) RemoveInvalidEdges saturated an arc, by iteration parity
@@ -2034,39 +2037,61 @@ struct PolicyJob {
 };
 
 // Features of a batch and the policy decision for the k_solve launch that
-// follows (JOB_AUTO).  One CTA of 256 threads: block reductions over the batch
-// entries, then the 12 features, then the plain rule (dynamic repair when the
-// batch holds at most 1 % of the edges, KERNELCYCLES = average degree) or the
-// network, with the plain rule as fallback on any non-finite or out-of-range
-// input (|z| > 8).  Entries with bad ids are skipped here; k_solve rejects
-// the batch.
+// follows (JOB_AUTO).  CTAs of 256 threads stride over the batch entries and
+// add their integer sums (exact, so the result does not depend on the order)
+// to the control block; the last CTA to arrive computes the 12 features,
+// then the plain rule (dynamic repair when the batch holds at most 1 % of
+// the edges, KERNELCYCLES = average degree) or the network, with the plain
+// rule as fallback on any non-finite or out-of-range input (|z| > 8), and
+// clears the sums for the next launch.  Entries with bad ids are skipped
+// here; k_solve rejects the batch.
 __global__ void __launch_bounds__(256) k_policy(DevGraph G, PolicyJob PJ) {
     Ctl *C = G.ctl;
     if (PJ.k_dev) PJ.k = lcg(PJ.k_dev);
-    __shared__ float red[3][256];
+    __shared__ long long red[3][8];
     __shared__ float x[mlp::kIn], z[mlp::kIn], h1[mlp::kH1], h2[mlp::kH2], y[mlp::kOut];
-    __shared__ int fb;
-    float inc = 0.f, touch = 0.f, sumd = 0.f;
-    for (int i = threadIdx.x; i < PJ.k; i += blockDim.x) {
+    __shared__ int fb, last;
+    long long inc = 0, touch = 0, sumd = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < PJ.k;
+         i += (long long)gridDim.x * blockDim.x) {
         const int id = PJ.ids[i];
         if (id < 0 || id >= G.m) continue;
         const long long old = lcg(&G.cap_edge[id]);
         long long nc = PJ.caps[i];
         if (PJ.flags & MF_DELTA) nc = old + nc < 0 ? 0 : old + nc;
-        inc += nc > old ? 1.f : 0.f;
-        sumd += (float)(nc > old ? nc - old : old - nc);
+        inc += nc > old;
+        sumd += nc > old ? nc - old : old - nc;
         const int a = __ldg(&G.arc_of_edge[id]);
-        if (a >= 0 && (__ldg(&G.head[a]) == G.t || __ldg(&G.head[__ldg(&G.rev[a])]) == G.s)) touch += 1.f;
+        if (a >= 0 && (__ldg(&G.head[a]) == G.t || __ldg(&G.head[__ldg(&G.rev[a])]) == G.s)) ++touch;
     }
-    red[0][threadIdx.x] = inc;
-    red[1][threadIdx.x] = touch;
-    red[2][threadIdx.x] = sumd;
+    inc = warp_sum(inc);
+    touch = warp_sum(touch);
+    sumd = warp_sum(sumd);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = inc;
+        red[1][threadIdx.x >> 5] = touch;
+        red[2][threadIdx.x >> 5] = sumd;
+    }
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o)
-            for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + o];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 3; ++q) {
+            long long v = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[q][w];
+            if (v) add_ll(&C->pol_acc[q], v);
+        }
+        __threadfence();
+        last = atomicAdd(&C->pol_done, 1) == (int)gridDim.x - 1;
+        if (last) {
+            __threadfence();
+            for (int q = 0; q < 3; ++q) {
+                red[q][0] = __ldcg(&C->pol_acc[q]);
+                C->pol_acc[q] = 0;
+            }
+            C->pol_done = 0;
+        }
     }
+    __syncthreads();
+    if (!last) return;
     if (threadIdx.x == 0) {
         const float n = (float)G.n, m = (float)(G.m > 0 ? G.m : 1), k = (float)PJ.k;
         const float kk = k > 0.f ? k : 1.f;
@@ -2076,9 +2101,9 @@ __global__ void __launch_bounds__(256) k_policy(DevGraph G, PolicyJob PJ) {
         x[1] = log2f(m);
         x[2] = log2f(1.f + k);
         x[3] = k / m;
-        x[4] = red[0][0] / kk;
-        x[5] = red[1][0] / kk;
-        x[6] = log2f(1.f + red[2][0]);
+        x[4] = (float)red[0][0] / kk;
+        x[5] = (float)red[1][0] / kk;
+        x[6] = log2f(1.f + (float)red[2][0]);
         const long long fl = lcg(&C->flow);
         x[7] = log2f(1.f + (float)(fl < 0 ? -fl : fl));
         x[8] = (float)G.A / n;
@@ -2330,7 +2355,7 @@ int launch_policy(mf_graph *g, int64_t k, const int *ids, const int *caps, int f
     pj.ids = ids;
     pj.caps = caps;
     pj.params = g->params;
-    k_policy<<<1, 256, 0, st>>>(g->dg, pj);
+    k_policy<<<g->grid, 256, 0, st>>>(g->dg, pj);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(MF_ECUDA, std::string("policy launch: ") + cudaGetErrorString(e));
     return MF_OK;
@@ -2642,7 +2667,7 @@ int mf_apply_updates_dev(mf_graph *g, const int32_t *k_dev, int64_t k_max, const
         pj.ids = edge_id;
         pj.caps = new_cap;
         pj.params = g->params;
-        k_policy<<<1, 256, 0, st>>>(g->dg, pj);
+        k_policy<<<g->grid, 256, 0, st>>>(g->dg, pj);
         MF_CUDA(cudaGetLastError());
         j.kind = JOB_AUTO;
     }
