@@ -3,8 +3,8 @@
 // The whole solve / repair of one graph is ONE persistent cooperative kernel
 // (k_solve): every CTA of one full wave runs the phases below in lock-step,
 // separated by a bounded grid barrier, so the data-dependent loops (BFS
-// levels, the push/relabel rounds) never return to the host (the paper keeps
-// termination on the GPU "without CPU intervention", Sec. 3):
+// levels, the push/relabel rounds) never return to the host (the paper also
+// decides termination on the device, Sec. 3):
 //
 //   validate batch -> apply capacity changes (Alg. 5, lines 1-3)
 //   -> clamp negative residuals (Alg. 5, lines 4-11)
@@ -30,6 +30,11 @@
 //
 // Mutable arrays are read with ld.global.cg (L2, coherent across SMs): the
 // persistent kernel never relies on L1 contents across a grid barrier.
+//
+// The phases avoid atomics that the whole grid aims at one address: the
+// items of a phase are dealt to the warps by a fixed stride (no work
+// tickets), and each warp stages the BFS frontier it discovers in shared
+// memory and publishes it a stage at a time.
 #include <cuda_runtime.h>
 
 #include <algorithm>
