@@ -182,6 +182,7 @@ struct DevGraph {
     int *rl;                  // vertices relabelled in the current loop iteration
     unsigned char *part;      // push-pull partition per vertex (kPartT / kPartS / kPartP), or null
     Ctl *ctl;
+    int al16;                 // head, r and rr start on 16-byte boundaries (16-byte staging copies)
 };
 
 // Push-pull partitions (Alg. 8): T can reach a sink, S cannot (the previous
@@ -310,9 +311,11 @@ __device__ __forceinline__ bool grid_sync(Ctl *C) {
 }
 
 // ---------------------------------------------------------- BFS visiting --
+// Per-thread work counters (32-bit to spare registers; added to the 64-bit
+// statistics after every loop iteration and at the end of the kernel).
 struct Counters {
-    long long bfs_arcs = 0, bfs_verts = 0, pr_arcs = 0, push = 0, relabel = 0, ri_arcs = 0,
-              ri_moves = 0, clamped = 0, resat = 0;
+    unsigned bfs_arcs = 0, bfs_verts = 0, pr_arcs = 0, push = 0, relabel = 0, ri_arcs = 0,
+             ri_moves = 0, clamped = 0, resat = 0;
 };
 
 constexpr int kIlp = 4;    // arcs in flight per lane in PushRelabel and RemoveInvalidEdges
@@ -352,15 +355,19 @@ __device__ __forceinline__ void warp_append_n(const bool (&pred)[N], const int (
 }
 
 constexpr int kWq = 320;   // staged frontier entries per warp (24 warps: 7680 ints)
+constexpr int kFl = 4;     // staged entries per lane in flight when a stage is published
 
 // The next BFS frontier as one warp writes it.  In grid-wide levels the
 // entries are staged in the warp's kWq ints of shared memory and reach the
-// global queue buf a whole stage at a time (one reservation on cnt), and the
-// arc total is summed in a register: the two counters every warp of the grid
-// shares then take one atomic per stage instead of one per round of arcs.
-// front_flush must run before the level's grid barrier.  In CTA 0's
-// small-frontier levels (stage == nullptr) entries go straight to the shared
-// frontier (positions >= cap to spill) and the arc total to its counter.
+// global queue buf a whole stage at a time (one reservation on cnt); the
+// bookkeeping of the staged vertices (their degrees for the frontier's arc
+// total, their excess for the active lists) is done when the stage is
+// published, for up to 32 kFl vertices at once, instead of inside the arc
+// scan that discovered them: the scan's chain of dependent accesses ends at
+// the height CAS.  front_flush must run before the level's grid barrier.  In
+// CTA 0's small-frontier levels (stage == nullptr) entries go straight to the
+// shared frontier (positions >= cap to spill) with their bookkeeping done at
+// once, and the arc total goes to its counter.
 struct Front {
     int *cnt, *buf;
     long long *asum;
@@ -371,32 +378,64 @@ struct Front {
     long long ds;   // arc total not yet added (warp-uniform)
 };
 
-__device__ __forceinline__ void front_flush_entries(Front &F) {
+// Publish the staged entries and do their bookkeeping: each joins the global
+// frontier, its degree counts towards the frontier's arc total, and a vertex
+// with positive excess (in the first stage of a push-pull repair, a deficient
+// vertex of the pull side) is active: worklist (degree <= kHubDeg) or hub
+// list.  All 32 lanes call.
+__device__ __forceinline__ void front_flush_entries(const DevGraph &G, Front &F, bool dual, Counters &K) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
     int base = 0;
     if (lane == 0) base = atomicAdd(F.cnt, F.sn);
     base = __shfl_sync(kFull, base, 0);
-    for (int i = lane; i < F.sn; i += 32) F.buf[base + i] = F.stage[i];
+    long long ds = 0;
+    for (int i0 = 0; i0 < F.sn; i0 += 32 * kFl) {
+        int v[kFl], deg[kFl];
+        long long ev[kFl];
+        bool ok[kFl], small[kFl], hub[kFl];
+#pragma unroll
+        for (int j = 0; j < kFl; ++j) {
+            const int i = i0 + 32 * j + lane;
+            ok[j] = i < F.sn;
+            v[j] = ok[j] ? F.stage[i] : 0;
+            if (ok[j]) F.buf[base + i] = v[j];
+        }
+#pragma unroll
+        for (int j = 0; j < kFl; ++j) {
+            deg[j] = ok[j] ? __ldg(&G.row[v[j] + 1]) - __ldg(&G.row[v[j]]) : 0;
+            ev[j] = ok[j] ? lcg(&G.e[v[j]]) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kFl; ++j) {
+            // a vertex of the pull side (forward search) is active when deficient
+            const bool pull = ok[j] && dual && G.part[v[j]] == kPartS;
+            const bool act = ok[j] && (pull ? ev[j] < 0 : ev[j] > 0);
+            ds += deg[j];
+            K.bfs_verts += ok[j];
+            hub[j] = act && deg[j] > kHubDeg;
+            small[j] = act && !hub[j];
+        }
+        warp_append_n(small, v, &G.ctl->wcnt, G.wl);
+        warp_append_n(hub, v, &G.ctl->hcnt, G.hl);
+    }
+    F.ds += warp_sum(ds);
     __syncwarp();
     F.sn = 0;
 }
 
 // Publish what the warp has staged.  All 32 lanes call.
-__device__ __forceinline__ void front_flush(Front &F) {
-    if (F.stage && F.sn) front_flush_entries(F);
+__device__ __forceinline__ void front_flush(const DevGraph &G, Front &F, bool dual, Counters &K) {
+    if (F.stage && F.sn) front_flush_entries(G, F, dual, K);
     if (F.ds && (threadIdx.x & 31) == 0) add_ll(F.asum, F.ds);
     F.ds = 0;
 }
 
-// Append the lanes' flagged values of N slots (at most 32 N <= kWq
-// entries).  All 32 lanes call.
+// Stage the lanes' flagged values of N slots (at most 32 N <= kWq entries).
+// Only for grid-wide levels (F.stage set).  All 32 lanes call.
 template <int N>
-__device__ __forceinline__ void front_append_n(const bool (&pred)[N], const int (&val)[N], Front &F) {
-    if (!F.stage) {
-        warp_append_n(pred, val, F.cnt, F.buf, F.cap, F.spill);
-        return;
-    }
+__device__ __forceinline__ void front_stage_n(const DevGraph &G, const bool (&pred)[N], const int (&val)[N],
+                                              Front &F, bool dual, Counters &K) {
     const unsigned below = (1u << (threadIdx.x & 31)) - 1u;
     unsigned m[N];
     int tot = 0;
@@ -406,7 +445,7 @@ __device__ __forceinline__ void front_append_n(const bool (&pred)[N], const int 
         tot += __popc(m[j]);
     }
     if (tot == 0) return;
-    if (F.sn + tot > kWq) front_flush_entries(F);
+    if (F.sn + tot > kWq) front_flush_entries(G, F, dual, K);
     int base = F.sn;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
@@ -416,20 +455,21 @@ __device__ __forceinline__ void front_append_n(const bool (&pred)[N], const int 
     F.sn = base;
 }
 
-__device__ __forceinline__ void front_add_arcs(Front &F, long long ds) {
-    if (F.stage) F.ds += ds;
-    else if ((threadIdx.x & 31) == 0 && ds) add_ll(F.asum, ds);
-}
-
-// bfs_discovered for kIlpB slots per lane at once: the loads of all slots are
-// issued together and each list gets one reservation per warp.
+// bfs_discovered for kIlpB slots per lane at once.  Grid-wide levels stage
+// the vertices (bookkeeping when the stage is published); CTA 0's levels do
+// the bookkeeping here, the loads of all slots issued together and each list
+// getting one reservation per warp.
 __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (&disc)[kIlpB], const int (&v)[kIlpB],
                                                  unsigned fwd, bool dual, Front &F, Counters &K) {
     bool any = false;
 #pragma unroll
     for (int j = 0; j < kIlpB; ++j) any |= disc[j];
     if (!__any_sync(kFull, any)) return;
-    front_append_n(disc, v, F);
+    if (F.stage) {
+        front_stage_n(G, disc, v, F, dual, K);
+        return;
+    }
+    warp_append_n(disc, v, F.cnt, F.buf, F.cap, F.spill);
     int deg[kIlpB];
     long long ev[kIlpB];
 #pragma unroll
@@ -448,37 +488,20 @@ __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (
         hub[j] = act && deg[j] > kHubDeg;
         small[j] = act && !hub[j];
     }
-    front_add_arcs(F, warp_sum(ds));
+    ds = warp_sum(ds);
+    if ((threadIdx.x & 31) == 0 && ds) add_ll(F.asum, ds);
     warp_append_n(small, v, &G.ctl->wcnt, G.wl);
     warp_append_n(hub, v, &G.ctl->hcnt, G.hl);
 }
 
-// Bookkeeping of a vertex v reached at the next level (disc): it joins the
-// next frontier, its degree counts towards that frontier's arc total, and
-// with positive excess it is active: worklist (degree <= kHubDeg) or hub
-// list.  All 32 lanes call.
+// Bookkeeping of a vertex v reached at the next level (disc), one slot per
+// lane: as bfs_discovered_n.  All 32 lanes call.
 __device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int v, bool fwd, bool dual,
                                                Front &F, Counters &K) {
-    if (!__ballot_sync(kFull, disc)) return;
-    {
-        const bool p[1] = {disc};
-        const int x[1] = {v};
-        front_append_n(p, x, F);
-    }
-    int deg = 0;
-    bool act = false;
-    if (disc) {
-        deg = __ldg(&G.row[v + 1]) - __ldg(&G.row[v]);
-        const long long ev = lcg(&G.e[v]);
-        act = fwd ? ev < 0 : ev > 0;
-        ++K.bfs_verts;
-    }
-    front_add_arcs(F, warp_sum((long long)deg));
-    if (__ballot_sync(kFull, act)) {
-        const bool hub = act && deg > kHubDeg;
-        warp_append(act && !hub, v, &G.ctl->wcnt, G.wl);
-        warp_append(hub, v, &G.ctl->hcnt, G.hl);
-    }
+    const bool d1[kIlpB] = {disc, false, false, false};
+    const int v1[kIlpB] = {v, 0, 0, 0};
+    static_assert(kIlpB == 4, "single-slot form of bfs_discovered_n");
+    bfs_discovered_n(G, d1, v1, fwd ? 1u : 0u, dual, F, K);
 }
 
 // Backward BFS step over kIlpB arcs per lane (a[j] of frontier vertex u, head
@@ -652,26 +675,37 @@ __device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item,
 }
 
 // ------------------------------------------------------ push / relabel --
-// One push of d units along arc a (u -> v): both residual copies of the arc
-// pair and the head's excess; the caller subtracts the total from e(u).
-__device__ __forceinline__ long long push_arc(const DevGraph &G, int a, int v, int d) {
-    const int b = __ldg(&G.rev[a]);
+// One push of d units along arc a (u -> v) with reverse arc b: both residual
+// copies of the arc pair (reductions: nothing waits on them) and the head's
+// excess; the caller subtracts the total from e(u).  Returns e(v) before.
+// A push into s or t (never active) is a reduction too: the pusher does not
+// wait in the queue of same-address atomics that the many pushes into the
+// sink form at its L2 slice.
+__device__ __forceinline__ long long push_arc(const DevGraph &G, int a, int b, int v, int d) {
     atomicSub(&G.r[a], d);
     atomicSub(&G.rr[b], d);
     atomicAdd(&G.r[b], d);
     atomicAdd(&G.rr[a], d);
+    if (v == G.t || v == G.s) {
+        add_ll(&G.e[v], d);
+        return 1;
+    }
     return (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&G.e[v]), (unsigned long long)d);
 }
 
-// One pull of d units into u along arc a (u -> v) of u's list: the arc
-// v -> u loses d of residual and v loses d of excess (PullRelabel, Alg. 6);
-// the caller adds the total to e(u).  Returns e(v) before the pull.
-__device__ __forceinline__ long long pull_arc(const DevGraph &G, int a, int v, int d) {
-    const int b = __ldg(&G.rev[a]);
+// One pull of d units into u along arc a (u -> v) of u's list, reverse arc
+// b: the arc v -> u loses d of residual and v loses d of excess
+// (PullRelabel, Alg. 6); the caller adds the total to e(u).  Returns e(v)
+// before the pull.
+__device__ __forceinline__ long long pull_arc(const DevGraph &G, int a, int b, int v, int d) {
     atomicSub(&G.r[b], d);
     atomicSub(&G.rr[a], d);
     atomicAdd(&G.r[a], d);
     atomicAdd(&G.rr[b], d);
+    if (v == G.t || v == G.s) {
+        add_ll(&G.e[v], -(long long)d);
+        return -1;
+    }
     return (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&G.e[v]), (unsigned long long)(-(long long)d));
 }
 
@@ -696,57 +730,19 @@ __device__ __forceinline__ void note_relabel(const DevGraph &G, int u, unsigned 
     if (atomicExch(&G.rstamp[u], rstamp) != rstamp) G.rl[atomicAdd(&G.ctl->rlcnt, 1)] = u;
 }
 
-// The kIlp moves of a round (d[j] > 0: d[j] units along slot j to v[j],
-// whose excess was old[j]): a push that raised e(v) above 0 (a pull that
-// lowered it below 0) turned v active, and v (not s or t, below height n)
-// joins the next activation round when its degree is <= kHubDeg, else the
-// hub list of the next PushRelabel pass.  The loads and stamps of all slots
-// are issued together, and each list gets one reservation per warp.  All 32
-// lanes call.
-template <bool PULL>
-__device__ __forceinline__ void note_activation_n(const DevGraph &G, const int (&d)[kIlp], const int (&v)[kIlp],
-                                                  const long long (&old)[kIlp], const ActList &AL) {
-    bool cand[kIlp];
-    bool any = false;
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
-        const bool turned = PULL ? (old[j] >= 0 && old[j] - d[j] < 0) : (old[j] <= 0 && old[j] + d[j] > 0);
-        cand[j] = d[j] > 0 && turned && v[j] != G.s && v[j] != G.t;
-        any |= cand[j];
-    }
-    if (!__any_sync(kFull, any)) return;
-    int hv[kIlp], deg[kIlp];
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
-        hv[j] = cand[j] ? lcg(&G.h[v[j]]) : G.n;
-        deg[j] = cand[j] ? __ldg(&G.row[v[j] + 1]) - __ldg(&G.row[v[j]]) : 0;
-    }
-    bool add[kIlp], add_hub[kIlp];
-#pragma unroll
-    for (int j = 0; j < kIlp; ++j) {
-        add[j] = add_hub[j] = false;
-        if (hv[j] < G.n) {
-            if (deg[j] <= kHubDeg)
-                add[j] = atomicExch(&G.astamp[v[j]], AL.stamp) != AL.stamp;
-            else
-                add_hub[j] = atomicExch(&G.astamp[v[j]], AL.hstamp) != AL.hstamp;
-        }
-    }
-    warp_append_n(add, v, AL.cnt, AL.list);
-    warp_append_n(add_hub, v, AL.hcnt, AL.hlist);
-}
-
 // One round of a warp's arc scan: lane i holds arcs a0 + 32 j + i (j < kIlp)
-// with their residual (0 past `end`), head and the head's height.  All loads
-// of the round are issued before any is used.
+// with their residual (0 past `end`), head and the head's height, and, when
+// the round is one to push along (REV), the reverse arcs of its residual
+// arcs.  All loads of the round are issued before any is used; the reverse
+// arcs load beside the heights.
 struct ArcRound {
-    int ra[kIlp], v[kIlp], hv[kIlp];
+    int ra[kIlp], v[kIlp], hv[kIlp], rb[kIlp];
 };
 
 // The residual is that of the arc u -> head (push) or head -> u (pull, the
 // mirror rr).  With a partition array pt, an arc to a vertex of another part
 // counts as absent (push-pull: each side works on its own vertices only).
-template <bool PULL>
+template <bool PULL, bool REV>
 __device__ __forceinline__ void load_round_t(const DevGraph &G, int a0, int end, ArcRound &R,
                                              const unsigned char *pt, unsigned char side) {
     const int lane = threadIdx.x & 31;
@@ -763,11 +759,10 @@ __device__ __forceinline__ void load_round_t(const DevGraph &G, int a0, int end,
             if (R.ra[j] > 0 && pt[R.v[j]] != side) R.ra[j] = 0;
     }
 #pragma unroll
-    for (int j = 0; j < kIlp; ++j) R.hv[j] = R.ra[j] > 0 ? lcg(&G.h[R.v[j]]) : 0;
-}
-
-__device__ __forceinline__ void load_round(const DevGraph &G, int a0, int end, ArcRound &R) {
-    load_round_t<false>(G, a0, end, R, nullptr, 0);
+    for (int j = 0; j < kIlp; ++j) {
+        R.hv[j] = R.ra[j] > 0 ? lcg(&G.h[R.v[j]]) : 0;
+        R.rb[j] = (REV && R.ra[j] > 0) ? __ldg(&G.rev[a0 + 32 * j + lane]) : 0;
+    }
 }
 
 __device__ __forceinline__ int round_arcs(int a0, int end) {
@@ -793,21 +788,266 @@ __device__ __forceinline__ unsigned long long round_min_key(const ArcRound &R, i
     return best;
 }
 
+// The amount moved along arc a (u -> v, reverse b) in one step: a push or a
+// pull.
+template <bool PULL>
+__device__ __forceinline__ long long move_arc(const DevGraph &G, int a, int b, int v, int d) {
+    return PULL ? pull_arc(G, a, b, v, d) : push_arc(G, a, b, v, d);
+}
+
+// The amounts of one round at height hh, in arc order (round slot j, then
+// lane), as consecutive Alg. 2 steps would move them: min(rem, c_f) each
+// until rem is used up; tot receives the round's residual at height hh.
+__device__ __forceinline__ void round_amounts(const ArcRound &R, int hh, long long rem, int (&d)[kIlp],
+                                              long long &tot) {
+    tot = 0;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        const int ra = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
+        const long long incl = warp_incl_scan(ra) + tot;
+        const long long dj = rem - (incl - ra);
+        d[j] = dj < 0 ? 0 : (dj > ra ? ra : (int)dj);
+        tot = __shfl_sync(kFull, incl, 31);
+    }
+}
+
+// The moves of one round (d[j] > 0: d[j] units along slot j of R, a round
+// loaded with its reverse arcs), and the filing of the vertices they turn
+// active: a push that raised e(v) above 0 (a pull that lowered it below 0)
+// makes v active, and v (not s or t) joins the next activation round when its
+// degree is <= kHubDeg, else the hub list of the next PushRelabel pass.  The
+// heads' degrees load beside the move atomics, so the filing waits once for
+// both; v's height is the one the scan read (a push only goes below h(u) <
+// n).  Each list gets one reservation per warp.  Returns this lane's total
+// moved.  All 32 lanes call.
+template <bool PULL>
+__device__ __forceinline__ long long move_round(const DevGraph &G, int a0, const int (&d)[kIlp], const ArcRound &R,
+                                                const ActList &AL, Counters &K) {
+    const int lane = threadIdx.x & 31;
+    long long old[kIlp], sent = 0;
+    int deg[kIlp];
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        old[j] = 0;
+        deg[j] = 0;
+        if (d[j] > 0) {
+            old[j] = move_arc<PULL>(G, a0 + 32 * j + lane, R.rb[j], R.v[j], d[j]);
+            deg[j] = __ldg(&G.row[R.v[j] + 1]) - __ldg(&G.row[R.v[j]]);
+            sent += d[j];
+            ++K.push;
+        }
+    }
+    bool add[kIlp], add_hub[kIlp];
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < kIlp; ++j) {
+        const bool turned = PULL ? (old[j] >= 0 && old[j] - d[j] < 0) : (old[j] <= 0 && old[j] + d[j] > 0);
+        const bool cand = d[j] > 0 && turned && R.v[j] != G.s && R.v[j] != G.t;
+        add[j] = cand && deg[j] <= kHubDeg;
+        add_hub[j] = cand && deg[j] > kHubDeg;
+        any |= cand;
+    }
+    if (__any_sync(kFull, any)) {
+#pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            if (add[j]) add[j] = atomicExch(&G.astamp[R.v[j]], AL.stamp) != AL.stamp;
+            if (add_hub[j]) add_hub[j] = atomicExch(&G.astamp[R.v[j]], AL.hstamp) != AL.hstamp;
+        }
+        warp_append_n(add, R.v, AL.cnt, AL.list);
+        warp_append_n(add_hub, R.v, AL.hcnt, AL.hlist);
+    }
+    return sent;
+}
+
+// ------------------------------------------------ staged arc ranges --
+// A warp that scans the arcs of one vertex of degree 129 .. kStg copies them
+// to its own shared memory first: residuals and heads as 16-byte cp.async
+// copies (L2 only, so residuals written by other SMs' atomics are seen; no
+// register holds an arc in flight), then the heights of the residual arcs'
+// heads, gathered kGat per lane at a time.  A range of up to kStg arcs then
+// takes three dependent round trips to memory instead of two per 128-arc
+// round.  The staged range starts at the 16-byte boundary at or below the
+// first arc: index i of a stage is arc (a0 & ~3) + i.
+constexpr int kStg = 512;              // arcs one warp stages at a time
+constexpr int kStgInts = kStg + 8;     // + the alignment slack of the first copy
+constexpr int kStgWarp = 3 * kStgInts; // ints per warp: heads, residuals, heights
+constexpr int kGat = 8;                // height gathers in flight per lane
+static_assert(kHubDeg <= kStg, "a worklist vertex fits one stage");
+constexpr int kDynSmem = (kBlock / 32) * kStgWarp * 4;   // bytes of dynamic shared memory of k_solve
+
+__device__ __forceinline__ void cp_async16(int *dst, const int *src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+// Copy arcs [a0, a1) of the int array src (A entries) to dst[i], i = a -
+// (a0 & ~3): 16 bytes per copy, except where the array is not 16-byte aligned
+// or the copy would pass its end (plain L2 loads there).  Pair with
+// stage_wait.  All 32 lanes call.
+__device__ __forceinline__ void stage_copy(const int *src, int *dst, int a0, int a1, long long A, bool al16) {
+    const int base = a0 & ~3;
+    const int nch = (a1 - base + 3) >> 2;
+    for (int c = threadIdx.x & 31; c < nch; c += 32) {
+        const long long a = base + 4LL * c;
+        if (al16 && a + 4 <= A) {
+            cp_async16(dst + 4 * c, src + a);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (a + q < A) dst[4 * c + q] = __ldcg(src + a + q);
+        }
+    }
+}
+
+// Wait for this lane's copies, then make every lane's visible to the warp.
+__device__ __forceinline__ void stage_wait() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+}
+
+// Heights of the heads of the staged residual arcs in [a0, a1): sh[i] = h of
+// the head, or INT_MAX for no residual arc (out of range, zero residual, or,
+// with a partition array pt, a head in another part: its residual is zeroed
+// in sr).  Returns this lane's lowest (height, arc - a0) key.
+__device__ __forceinline__ unsigned long long stage_heights(const DevGraph &G, const int *sv, int *sr, int *sh,
+                                                            int a0, int a1, const unsigned char *pt,
+                                                            unsigned char side) {
+    const int lane = threadIdx.x & 31;
+    const int base = a0 & ~3, cnt = a1 - base;
+    unsigned long long best = ~0ull;
+    for (int i0 = lane; i0 < cnt; i0 += 32 * kGat) {
+        int hv[kGat];
+        bool res[kGat];
+        unsigned char pv[kGat];
+#pragma unroll
+        for (int j = 0; j < kGat; ++j) {
+            const int i = i0 + 32 * j;
+            res[j] = i < cnt && base + i >= a0 && sr[i] > 0;
+            const int v = res[j] ? sv[i] : 0;
+            hv[j] = res[j] ? lcg(&G.h[v]) : 0;
+            pv[j] = (pt && res[j]) ? pt[v] : side;
+        }
+#pragma unroll
+        for (int j = 0; j < kGat; ++j) {
+            const int i = i0 + 32 * j;
+            if (res[j] && pv[j] != side) {
+                res[j] = false;
+                sr[i] = 0;
+            }
+            if (i < cnt) sh[i] = res[j] ? hv[j] : INT_MAX;
+            if (res[j]) {
+                const unsigned long long key = ((unsigned long long)(unsigned)hv[j] << 32) | (unsigned)(base + i - a0);
+                best = key < best ? key : best;
+            }
+        }
+    }
+    __syncwarp();
+    return best;
+}
+
+// The moves of N slots per lane (d[j] > 0: d[j] units along arc a[j] of u,
+// reverse b[j], head v[j]) and the filing of the vertices they turn active,
+// as move_round.  Returns this lane's total moved.  All 32 lanes call.
+constexpr int kMv = 4;   // moves in flight per lane
+template <bool PULL, int N>
+__device__ __forceinline__ long long move_batch(const DevGraph &G, const int (&a)[N], const int (&b)[N],
+                                                const int (&v)[N], const int (&d)[N], const ActList &AL,
+                                                Counters &K) {
+    long long old[N], sent = 0;
+    int deg[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        old[j] = 0;
+        deg[j] = 0;
+        if (d[j] > 0) {
+            old[j] = move_arc<PULL>(G, a[j], b[j], v[j], d[j]);
+            deg[j] = __ldg(&G.row[v[j] + 1]) - __ldg(&G.row[v[j]]);
+            sent += d[j];
+            ++K.push;
+        }
+    }
+    bool add[N], add_hub[N];
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const bool turned = PULL ? (old[j] >= 0 && old[j] - d[j] < 0) : (old[j] <= 0 && old[j] + d[j] > 0);
+        const bool cand = d[j] > 0 && turned && v[j] != G.s && v[j] != G.t;
+        add[j] = cand && deg[j] <= kHubDeg;
+        add_hub[j] = cand && deg[j] > kHubDeg;
+        any |= cand;
+    }
+    if (__any_sync(kFull, any)) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (add[j]) add[j] = atomicExch(&G.astamp[v[j]], AL.stamp) != AL.stamp;
+            if (add_hub[j]) add_hub[j] = atomicExch(&G.astamp[v[j]], AL.hstamp) != AL.hstamp;
+        }
+        warp_append_n(add, v, AL.cnt, AL.list);
+        warp_append_n(add_hub, v, AL.hcnt, AL.hlist);
+    }
+    return sent;
+}
+
+// The moves a decision to push at height hh makes along staged arcs [a0,
+// a1): the amounts in arc order (min(rem, c_f) each, 32 arcs a step, over
+// the arcs at height hh), written over the heights in sh, then all moves at
+// once, kGat per lane in flight.  Returns the warp's total moved (all lanes).
+template <bool PULL>
+__device__ __forceinline__ long long stage_moves(const DevGraph &G, const int *sv, const int *sr, int *sh, int a0,
+                                                 int a1, int hh, long long rem, const ActList &AL, Counters &K) {
+    const int lane = threadIdx.x & 31;
+    const int base = a0 & ~3, cnt = a1 - base;
+    int iend = 0;
+    for (int i0 = 0; i0 < cnt && rem > 0; i0 += 32) {
+        const int i = i0 + lane;
+        const int ra = (i < cnt && sh[i] == hh) ? sr[i] : 0;
+        const long long incl = warp_incl_scan(ra);
+        const long long dj = rem - (incl - ra);
+        if (i < cnt) sh[i] = dj < 0 ? 0 : (dj > ra ? ra : (int)dj);
+        rem -= min(__shfl_sync(kFull, incl, 31), rem);
+        iend = i0 + 32;
+    }
+    __syncwarp();
+    long long sent = 0;
+    const int lim = min(iend, cnt);
+    // warp-uniform trip count: move_batch holds warp-wide ballots
+    for (int i0 = 0; i0 < lim; i0 += 32 * kMv) {
+        int a[kMv], b[kMv], v[kMv], d[kMv];
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < kMv; ++j) {
+            const int i = i0 + 32 * j + lane;
+            d[j] = i < lim ? sh[i] : 0;
+            a[j] = base + i;
+            v[j] = d[j] > 0 ? sv[i] : 0;
+            b[j] = d[j] > 0 ? __ldg(&G.rev[a[j]]) : 0;
+            any |= d[j] > 0;
+        }
+        if (!__any_sync(kFull, any)) continue;
+        sent += move_batch<PULL, kMv>(G, a, b, v, d, AL, K);
+    }
+    return warp_sum(sent);
+}
+
 // Algorithm 2 on vertex u by one warp, up to kc cycles.  A cycle scans u's
 // arcs once for the lowest residual neighbour height h^ (ties: lowest arc;
 // heights read once per cycle, Note 3 of Sec. 3).  If h(u) > h^ the cycle
 // performs the pushes that consecutive Alg. 2 steps would make to the arcs at
-// height h^ -- in arc order, min(e, c_f) each, until e(u) is used up -- with a
-// second pass over the arcs; otherwise it relabels u to h^ + 1.  A vertex
-// without residual arcs gets height n.  Only u's warp lowers r(u, .) and e(u);
-// other warps only raise them, so every amount pushed is available.
-// With PULL the same steps are Algorithm 6 (PullRelabel) on a deficient u:
-// residual arcs into u, pulls of min(-e, c_f) from the lowest of them.
-// Still active after its steps: u takes part in the next round as well.
+// height h^ -- in arc order, min(e, c_f) each, until e(u) is used up --
+// (from the round the scan loaded when u has one round of arcs; vertices with
+// more reload the rounds that hold such an arc); otherwise it relabels u to
+// h^ + 1.  A vertex without residual arcs gets height n.  Only u's warp
+// lowers r(u, .) and e(u) and changes h(u) during a round; other warps only
+// raise r(u, .) and e(u), so every amount pushed is available, h(u) is read
+// once, and e(u) is re-read beside each cycle's arc loads.  With PULL the
+// same steps are Algorithm 6 (PullRelabel) on a deficient u: residual arcs
+// into u, pulls of min(-e, c_f) from the lowest of them.  Once its steps are
+// done u joins the iteration's relabel list if it was relabelled, and the
+// next round's list if still active.
 template <bool PULL>
-__device__ __forceinline__ void requeue_if_active_t(const DevGraph &G, int u, const ActList &AL) {
+__device__ __forceinline__ void pr_finish_t(const DevGraph &G, int u, int hu, bool relabelled, const ActList &AL) {
     if ((threadIdx.x & 31) == 0) {
-        const int hu = lcg(&G.h[u]);
+        if (relabelled) note_relabel(G, u, AL.rstamp);
         const long long eu = lcg(&G.e[u]);
         if (hu < G.n && (PULL ? eu < 0 : eu > 0) && atomicExch(&G.astamp[u], AL.stamp) != AL.stamp)
             AL.list[atomicAdd(AL.cnt, 1)] = u;
@@ -815,168 +1055,103 @@ __device__ __forceinline__ void requeue_if_active_t(const DevGraph &G, int u, co
     __syncwarp();
 }
 
-// The amount moved along arc a (u -> v) in one step: a push or a pull.
-template <bool PULL>
-__device__ __forceinline__ long long move_arc(const DevGraph &G, int a, int v, int d) {
-    return PULL ? pull_arc(G, a, v, d) : push_arc(G, a, v, d);
+// The cycle's decision after the scan: returns the height to push to, or -1
+// after a relabel (hu updated, h(u) written), or -2 when u is done.
+__device__ __forceinline__ int pr_decide(const DevGraph &G, int u, unsigned long long best, long long eu, int &hu,
+                                         bool &relabelled, Counters &K) {
+    if (eu <= 0) return -2;
+    if (best == ~0ull) {
+        hu = G.n;
+        if ((threadIdx.x & 31) == 0) {
+            G.h[u] = G.n;
+            ++K.relabel;
+        }
+        relabelled = true;
+        return -2;
+    }
+    const int hh = (int)(best >> 32);
+    if (hu <= hh) {
+        hu = hh + 1;
+        if ((threadIdx.x & 31) == 0) {
+            G.h[u] = hu;
+            ++K.relabel;
+        }
+        relabelled = true;
+        return -1;
+    }
+    return hh;
 }
 
-// push_relabel_warp for a vertex whose arcs fit in one round (<= 32 kIlp):
-// the round loaded for the lowest-neighbour scan also serves the pushes (the
-// heights are the ones read once for the step, and u's own residuals can only
-// have grown since).
+// u with one round of arcs (<= 32 kIlp)
 template <bool PULL>
 __device__ __forceinline__ void push_relabel_small_t(const DevGraph &G, int u, int beg, int end, int kc,
-                                                     const ActList &AL, const unsigned char *pt, unsigned char side,
-                                                     Counters &K) {
+                                                  const ActList &AL, const unsigned char *pt, unsigned char side,
+                                                  Counters &K) {
     const int lane = threadIdx.x & 31;
-    const int n = G.n;
-    for (int c = 0; c < kc; ++c) {
-        int hu = 0;
-        long long eu = 0;
-        if (lane == 0) {
-            hu = lcg(&G.h[u]);
-            eu = lcg(&G.e[u]);
-        }
-        hu = __shfl_sync(kFull, hu, 0);
-        eu = __shfl_sync(kFull, eu, 0);
-        if (PULL) eu = -eu;   // the deficit to fill
-        if (hu >= n || eu <= 0) break;
+    int hu = lcg(&G.h[u]);
+    bool relabelled = false;
+    for (int c = 0; c < kc && hu < G.n; ++c) {
+        long long eu = lcg(&G.e[u]);
         ArcRound R;
-        load_round_t<PULL>(G, beg, end, R, pt, side);
+        load_round_t<PULL, true>(G, beg, end, R, pt, side);
         K.pr_arcs += round_arcs(beg, end);
         const unsigned long long best = warp_min(round_min_key(R, beg, beg));
-        if (best == ~0ull) {
-            if (lane == 0) {
-                G.h[u] = n;
-                ++K.relabel;
-                note_relabel(G, u, AL.rstamp);
-            }
-            break;
-        }
-        const int hh = (int)(best >> 32);
-        if (hu <= hh) {
-            if (lane == 0) {
-                G.h[u] = hh + 1;
-                ++K.relabel;
-                note_relabel(G, u, AL.rstamp);
-            }
-            __syncwarp();
-            continue;
-        }
-        long long rem = eu, sent = 0, old[kIlp];
+        const int hh = pr_decide(G, u, best, PULL ? -eu : eu, hu, relabelled, K);
+        if (hh == -2) break;
+        if (hh == -1) continue;
         int d[kIlp];
-#pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            const int ra = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
-            const long long incl = warp_incl_scan(ra);
-            const long long dj = rem - (incl - ra);
-            d[j] = dj < 0 ? 0 : (dj > ra ? ra : (int)dj);
-            const long long tot = __shfl_sync(kFull, incl, 31);
-            rem -= tot < rem ? tot : rem;
-        }
-#pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            old[j] = 0;
-            if (d[j] > 0) {
-                old[j] = move_arc<PULL>(G, beg + 32 * j + lane, R.v[j], d[j]);
-                sent += d[j];
-                ++K.push;
-            }
-        }
-        note_activation_n<PULL>(G, d, R.v, old, AL);
-        sent = warp_sum(sent);
+        long long tot;
+        round_amounts(R, hh, PULL ? -eu : eu, d, tot);
+        const long long sent = warp_sum(move_round<PULL>(G, beg, d, R, AL, K));
         if (lane == 0 && sent) add_ll(&G.e[u], PULL ? sent : -sent);
         __syncwarp();
     }
-    requeue_if_active_t<PULL>(G, u, AL);
+    pr_finish_t<PULL>(G, u, hu, relabelled, AL);
+}
+
+// u with more than one round of arcs (<= kHubDeg): the arcs are staged in
+// the warp's shared memory (heads once, residuals and heights every cycle),
+// and the pushes go along the staged arcs at height h^ in arc order, 32 arcs
+// a step.
+template <bool PULL>
+__device__ __forceinline__ void push_relabel_staged_t(const DevGraph &G, int u, int beg, int end, int kc,
+                                                      const ActList &AL, const unsigned char *pt,
+                                                      unsigned char side, int *stg, Counters &K) {
+    const int lane = threadIdx.x & 31;
+    int *sv = stg, *sr = stg + kStgInts, *sh = stg + 2 * kStgInts;
+    stage_copy(G.head, sv, beg, end, G.A, G.al16);
+    int hu = lcg(&G.h[u]);
+    bool relabelled = false;
+    for (int c = 0; c < kc && hu < G.n; ++c) {
+        const long long eu = lcg(&G.e[u]);
+        stage_copy(PULL ? G.rr : G.r, sr, beg, end, G.A, G.al16);
+        stage_wait();
+        K.pr_arcs += (end - beg + 31 - lane) / 32;
+        const unsigned long long best = warp_min(stage_heights(G, sv, sr, sh, beg, end, pt, side));
+        const int hh = pr_decide(G, u, best, PULL ? -eu : eu, hu, relabelled, K);
+        if (hh == -2) break;
+        if (hh == -1) continue;
+        const long long sent = stage_moves<PULL>(G, sv, sr, sh, beg, end, hh, PULL ? -eu : eu, AL, K);
+        if (lane == 0 && sent) add_ll(&G.e[u], PULL ? sent : -sent);
+        __syncwarp();
+    }
+    pr_finish_t<PULL>(G, u, hu, relabelled, AL);
 }
 
 template <bool PULL>
 __device__ __forceinline__ void push_relabel_warp_t(const DevGraph &G, int u, int kc, const ActList &AL,
-                                                    const unsigned char *pt, unsigned char side, Counters &K) {
-    const int lane = threadIdx.x & 31;
-    const int n = G.n;
+                                                    const unsigned char *pt, unsigned char side, int *stg,
+                                                    Counters &K) {
     const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
-    if (end - beg <= 32 * kIlp) {
+    if (end - beg <= 32 * kIlp)
         push_relabel_small_t<PULL>(G, u, beg, end, kc, AL, pt, side, K);
-        return;
-    }
-    for (int c = 0; c < kc; ++c) {
-        int hu = 0;
-        long long eu = 0;
-        if (lane == 0) {
-            hu = lcg(&G.h[u]);
-            eu = lcg(&G.e[u]);
-        }
-        hu = __shfl_sync(kFull, hu, 0);
-        eu = __shfl_sync(kFull, eu, 0);
-        if (PULL) eu = -eu;
-        if (hu >= n || eu <= 0) break;
-        unsigned long long best = ~0ull;
-        for (int a0 = beg; a0 < end; a0 += 32 * kIlp) {
-            ArcRound R;
-            load_round_t<PULL>(G, a0, end, R, pt, side);
-            K.pr_arcs += round_arcs(a0, end);
-            const unsigned long long k = round_min_key(R, a0, beg);
-            best = k < best ? k : best;
-        }
-        best = warp_min(best);
-        if (best == ~0ull) {
-            if (lane == 0) {
-                G.h[u] = n;
-                ++K.relabel;
-                note_relabel(G, u, AL.rstamp);
-            }
-            break;
-        }
-        const int hh = (int)(best >> 32);
-        if (hu <= hh) {
-            if (lane == 0) {
-                G.h[u] = hh + 1;
-                ++K.relabel;
-                note_relabel(G, u, AL.rstamp);
-            }
-            __syncwarp();
-            continue;
-        }
-        long long rem = eu, sent = 0;
-        for (int a0 = beg; a0 < end && rem > 0; a0 += 32 * kIlp) {
-            ArcRound R;
-            load_round_t<PULL>(G, a0, end, R, pt, side);
-            K.pr_arcs += round_arcs(a0, end);
-            long long old[kIlp];
-            int d[kIlp];
-#pragma unroll
-            for (int j = 0; j < kIlp; ++j) {
-                const int ra = (R.ra[j] > 0 && R.hv[j] == hh) ? R.ra[j] : 0;
-                const long long incl = warp_incl_scan(ra);
-                const long long dj = rem - (incl - ra);
-                d[j] = dj < 0 ? 0 : (dj > ra ? ra : (int)dj);
-                const long long tot = __shfl_sync(kFull, incl, 31);
-                rem -= tot < rem ? tot : rem;
-            }
-#pragma unroll
-            for (int j = 0; j < kIlp; ++j) {
-                old[j] = 0;
-                if (d[j] > 0) {
-                    old[j] = move_arc<PULL>(G, a0 + 32 * j + lane, R.v[j], d[j]);
-                    sent += d[j];
-                    ++K.push;
-                }
-            }
-            note_activation_n<PULL>(G, d, R.v, old, AL);
-        }
-        sent = warp_sum(sent);
-        if (lane == 0 && sent) add_ll(&G.e[u], PULL ? sent : -sent);
-        __syncwarp();
-    }
-    requeue_if_active_t<PULL>(G, u, AL);
+    else
+        push_relabel_staged_t<PULL>(G, u, beg, end, kc, AL, pt, side, stg, K);
 }
 
-__device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int kc, const ActList &AL,
+__device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int kc, const ActList &AL, int *stg,
                                                   Counters &K) {
-    push_relabel_warp_t<false>(G, u, kc, AL, nullptr, 0, K);
+    push_relabel_warp_t<false>(G, u, kc, AL, nullptr, 0, stg, K);
 }
 
 // Algorithm 3 over the arcs [a0, a1) of vertex u (height hu) by one warp:
@@ -987,30 +1162,25 @@ __device__ __forceinline__ void push_relabel_warp(const DevGraph &G, int u, int 
 // Returns this lane's share of the excess moved out of u (PULL: into u).
 template <bool PULL>
 __device__ __forceinline__ long long remove_invalid_range_t(const DevGraph &G, int hu, int a0, int a1,
-                                                            int *moved_flag, const unsigned char *pt,
-                                                            unsigned char side, Counters &K) {
+                                                            const unsigned char *pt, unsigned char side,
+                                                            Counters &K) {
     const int lane = threadIdx.x & 31;
     long long moved = 0;
     for (int b0 = a0; b0 < a1; b0 += 32 * kIlp) {
         ArcRound R;
-        load_round_t<PULL>(G, b0, a1, R, pt, side);
+        load_round_t<PULL, false>(G, b0, a1, R, pt, side);
         K.ri_arcs += round_arcs(b0, a1);
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             if (R.ra[j] > 0 && hu > R.hv[j] + 1) {
-                move_arc<PULL>(G, b0 + 32 * j + lane, R.v[j], R.ra[j]);
+                const int a = b0 + 32 * j + lane;
+                move_arc<PULL>(G, a, __ldg(&G.rev[a]), R.v[j], R.ra[j]);
                 moved += R.ra[j];
                 ++K.ri_moves;
-                *moved_flag = 1;
             }
         }
     }
     return moved;
-}
-
-__device__ __forceinline__ long long remove_invalid_range(const DevGraph &G, int hu, int a0, int a1,
-                                                          int *moved_flag, Counters &K) {
-    return remove_invalid_range_t<false>(G, hu, a0, a1, moved_flag, nullptr, 0, K);
 }
 
 template <bool PULL>
@@ -1019,8 +1189,11 @@ __device__ __forceinline__ void remove_invalid_warp_t(const DevGraph &G, int u, 
     const int lane = threadIdx.x & 31;
     const int beg = __ldg(&G.row[u]), end = __ldg(&G.row[u + 1]);
     const int hu = __shfl_sync(kFull, lane == 0 ? lcg(&G.h[u]) : 0, 0);
-    const long long moved = warp_sum(remove_invalid_range_t<PULL>(G, hu, beg, end, moved_flag, pt, side, K));
-    if (lane == 0 && moved) add_ll(&G.e[u], PULL ? moved : -moved);
+    const long long moved = warp_sum(remove_invalid_range_t<PULL>(G, hu, beg, end, pt, side, K));
+    if (lane == 0 && moved) {
+        add_ll(&G.e[u], PULL ? moved : -moved);
+        *moved_flag = 1;   // once per warp
+    }
 }
 
 // Hub cycle helpers (the cooperative PushRelabel of high-degree vertices).
@@ -1033,7 +1206,7 @@ __device__ __forceinline__ unsigned long long hub_scan_item(const DevGraph &G, i
     unsigned long long best = ~0ull;
     for (; a0 < a1; a0 += 32 * kIlp) {
         ArcRound R;
-        load_round_t<PULL>(G, a0, a1, R, pt, side);
+        load_round_t<PULL, false>(G, a0, a1, R, pt, side);
         K.pr_arcs += round_arcs(a0, a1);
         const unsigned long long k = round_min_key(R, a0, beg);
         best = k < best ? k : best;
@@ -1054,9 +1227,9 @@ __device__ __forceinline__ long long hub_move_item(const DevGraph &G, int a0, in
         // the hub's excess may already be reserved by the items before this
         // one (not checked in the first push-pull stage, where scanning every
         // item measured faster: its pushes spread over the hub's arcs)
-        if (skip_done && __shfl_sync(kFull, lane == 0 ? lcg(rem) : 0ll, 0) <= 0) break;
+        if (skip_done && lcg(rem) <= 0) break;
         ArcRound R;
-        load_round_t<PULL>(G, a0, a1, R, pt, side);
+        load_round_t<PULL, true>(G, a0, a1, R, pt, side);
         K.pr_arcs += round_arcs(a0, a1);
         int ra[kIlp];
         long long incl[kIlp], tot = 0;
@@ -1072,22 +1245,30 @@ __device__ __forceinline__ long long hub_move_item(const DevGraph &G, int a0, in
             old = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(rem), (unsigned long long)(-tot));
         old = __shfl_sync(kFull, old, 0);
         if (old <= 0) break;
-        long long prev[kIlp];
         int d[kIlp];
 #pragma unroll
         for (int j = 0; j < kIlp; ++j) {
             const long long dj = old - (incl[j] - ra[j]);
             d[j] = dj < 0 ? 0 : (dj > ra[j] ? ra[j] : (int)dj);
-            prev[j] = 0;
-            if (d[j] > 0) {
-                prev[j] = move_arc<PULL>(G, a0 + 32 * j + lane, R.v[j], d[j]);
-                sent += d[j];
-                ++K.push;
-            }
         }
-        note_activation_n<PULL>(G, d, R.v, prev, AL);
+        sent += move_round<PULL>(G, a0, d, R, AL, K);
     }
     return warp_sum(sent);
+}
+
+// Add the warp's counters to the statistics st and clear them.  All 32 lanes
+// call.
+__device__ __forceinline__ void flush_counters(Counters &K, long long *st) {
+    const unsigned vals[9] = {K.bfs_verts, K.bfs_arcs, K.pr_arcs, K.push, K.relabel, K.ri_arcs, K.ri_moves,
+                              K.clamped, K.resat};
+    const int idx[9] = {S_BFS_VERTS, S_BFS_ARCS, S_PR_ARCS, S_PUSH, S_RELABEL, S_RI_ARCS, S_RI_MOVES, S_CLAMPED,
+                        S_RESAT};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const long long v = warp_sum((long long)vals[i]);
+        if ((threadIdx.x & 31) == 0 && v) add_ll(&st[idx[i]], v);
+    }
+    K = Counters{};
 }
 
 // ------------------------------------------------------------ the kernel --
@@ -1145,7 +1326,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     Counters K;
     // BFS frontiers in shared memory: CTA 0's small-frontier levels, and the
     // warps' staged entries in grid-wide levels (barriers keep them apart)
-    __shared__ __align__(16) int s_bfs[2 * kSoloCap];
+    // dynamic shared memory (kDynSmem bytes), used by one kind of phase at a
+    // time (grid barriers keep them apart): the BFS frontiers at its start,
+    // the warps' arc stages of PushRelabel
+    extern __shared__ __align__(16) int s_dyn[];
+    int *const s_bfs = s_dyn;
+    int *const stg = s_dyn + (threadIdx.x >> 5) * kStgWarp;
+    static_assert(2 * kSoloCap * 4 <= kDynSmem, "the shared frontiers exceed the dynamic shared memory");
     static_assert(kWq * (kBlock / 32) <= 2 * kSoloCap, "frontier stages exceed the shared frontier");
     static_assert(kWq >= 32 * kIlpB, "a stage holds one round of arcs");
     unsigned long long tprev = gtimer();
@@ -1210,6 +1397,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             return;
         }
         // c_f(u,v) += c'(u,v) - c(u,v)  (Alg. 5, lines 1-3)
+        bool blocks = false;   // this thread saw a decrement or an increment across the cut
         for (long long i = gtid; i < kb; i += gthreads) {
             const int eid = J.ids[i];
             const int nc = lcg(&J.newc[i]);
@@ -1226,10 +1414,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     // an increment can raise the flow only on an arc from
                     // the side that cannot reach a sink to the side that can
                     if (d < 0 || (lcg(&G.h[__ldg(&G.head[b])]) >= n && lcg(&G.h[__ldg(&G.head[a])]) < n))
-                        C->inc_block = 1;
+                        blocks = true;
                 }
             }
         }
+        // one store per warp: tens of thousands of same-address stores from
+        // every SM serialise at one L2 slice
+        if (__any_sync(kFull, blocks) && lane == 0) C->inc_block = 1;
         MF_SYNC(S_T_BATCH);
         // With the exact cut S = {h >= n} of the previous state (no residual
         // arc from S to T), increments on arcs that do not go from S to T
@@ -1564,7 +1755,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     bfs_expand_warp(G, beg, deg, fwd, dual, L, FR, K);
                 }
             }
-            front_flush(FR);
+            front_flush(G, FR, dual, K);
             MF_SYNC_T(S_T_BFS, L, bottom_up ? 2 : 0, cur);
             const int nch = lcg(ccnt);
             if (nch > 0) {
@@ -1587,7 +1778,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         bfs_visit_n(G, a, ok, fw, dual, L, FR, K);
                     }
                 }
-                front_flush(FR);
+                front_flush(G, FR, dual, K);
                 MF_SYNC_T(S_T_BFS, L, bottom_up ? 3 : 1, nch);
             }
             ++L;
@@ -1881,7 +2072,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             while (mask) {
                                 const int j = __ffs(mask) - 1;
                                 mask &= mask - 1u;
-                                push_relabel_warp(G, base + j, kc, AL, K);
+                                push_relabel_warp(G, base + j, kc, AL, stg, K);
                             }
                         }
                     } else if (stage == 1) {
@@ -1891,13 +2082,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             const int u = lcg(&list[i]);
                             const unsigned char side = G.part[u];
                             if (side == kPartS)
-                                push_relabel_warp_t<true>(G, u, kc, AL, G.part, side, K);
+                                push_relabel_warp_t<true>(G, u, kc, AL, G.part, side, stg, K);
                             else
-                                push_relabel_warp_t<false>(G, u, kc, AL, G.part, side, K);
+                                push_relabel_warp_t<false>(G, u, kc, AL, G.part, side, stg, K);
                         }
                     } else {
                         for (int i = gwarp; i < cnt; i += nwarps)
-                            push_relabel_warp(G, lcg(&list[i]), kc, AL, K);
+                            push_relabel_warp(G, lcg(&list[i]), kc, AL, stg, K);
                     }
                     MF_SYNC_T(S_T_PRW, rd, 0, cnt);
                     cnt = lcg(AL.cnt);
@@ -1937,16 +2128,21 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
             const unsigned char side = stage == 1 ? G.part[u] : (stage == 2 ? kPartP : kPartT);
             if (PP && side == kPartS) {
-                const long long got = warp_sum(
-                    remove_invalid_range_t<true>(G, hu, item.y, a1, &C->ri_moved[par], ptc, side, K));
-                if (lane == 0 && got) add_ll(&G.e[u], got);
+                const long long got = warp_sum(remove_invalid_range_t<true>(G, hu, item.y, a1, ptc, side, K));
+                if (lane == 0 && got) {
+                    add_ll(&G.e[u], got);
+                    C->ri_moved[par] = 1;
+                }
             } else {
-                const long long moved = warp_sum(
-                    remove_invalid_range_t<false>(G, hu, item.y, a1, &C->ri_moved[par], ptc, side, K));
-                if (lane == 0 && moved) add_ll(&G.e[u], -moved);
+                const long long moved = warp_sum(remove_invalid_range_t<false>(G, hu, item.y, a1, ptc, side, K));
+                if (lane == 0 && moved) {
+                    add_ll(&G.e[u], -moved);
+                    C->ri_moved[par] = 1;
+                }
             }
         }
         MF_SYNC_T(S_T_RI, 0, 0, nrl + nri);
+        flush_counters(K, ST);
 
         // Alg. 4's loop test, on the heights PushRelabel left: no vertex is
         // active if every activation was served (the last round's list is
@@ -2021,13 +2217,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         C->batch_err = 0;
         C->abort_loop = 0;
     }
-    long long vals[9] = {K.bfs_verts, K.bfs_arcs, K.pr_arcs, K.push, K.relabel, K.ri_arcs, K.ri_moves, K.clamped, K.resat};
-    const int idx[9] = {S_BFS_VERTS, S_BFS_ARCS, S_PR_ARCS, S_PUSH, S_RELABEL, S_RI_ARCS, S_RI_MOVES, S_CLAMPED, S_RESAT};
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const long long v = warp_sum(vals[i]);
-        if (lane == 0 && v) add_ll(&ST[idx[i]], v);
-    }
+    flush_counters(K, ST);
 }
 
 #undef ST
@@ -2256,6 +2446,23 @@ int set_err(int code, const std::string &msg) {
     return code;
 }
 
+// k_solve takes kDynSmem bytes of dynamic shared memory (above the default
+// 48 KB limit): both instances get the attribute once per device, before
+// their first occupancy query or launch on it.
+std::once_flag g_smem_once[kNoAllocMaxDevices];
+cudaError_t g_smem_err[kNoAllocMaxDevices];
+
+cudaError_t solve_kernels_prepare(int dev) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(g_smem_once[dev], [dev]() {
+        cudaError_t e = cudaFuncSetAttribute(k_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+        g_smem_err[dev] = e;
+    });
+    return g_smem_err[dev];
+}
+
 #define MF_CUDA(call)                                                                       \
     do {                                                                                    \
         cudaError_t e_ = (call);                                                            \
@@ -2341,7 +2548,7 @@ int launch(mf_graph *g, const Job &job, cudaStream_t st) {
         jb.sink_sat = 1;
     }
     const void *fn = job.pp ? (const void *)k_solve<true> : (const void *)k_solve<false>;
-    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(g->grid), dim3(kBlock), args, 0, st);
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(g->grid), dim3(kBlock), args, kDynSmem, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_err(MF_ECUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));
@@ -2501,8 +2708,9 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     if (!coop) return fail(MF_ECUDA, "device does not support cooperative launch");
     int per_sm = 0;
     int per_sm_pp = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<false>, kBlock, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_pp, k_solve<true>, kBlock, 0) != cudaSuccess)
+    if (solve_kernels_prepare(g->dev) != cudaSuccess) return fail(MF_ECUDA, "shared-memory attribute of k_solve");
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<false>, kBlock, kDynSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_pp, k_solve<true>, kBlock, kDynSmem) != cudaSuccess)
         return fail(MF_ECUDA, "occupancy query failed");
     per_sm = std::min(per_sm, per_sm_pp);
     if (per_sm < 1)
@@ -2547,6 +2755,10 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     D.part = g->opt.mode == MF_MODE_PUSH_PULL ? dnew<unsigned char>(g, N) : nullptr;
     D.ctl = dnew<Ctl>(g, 1);
     g->side_buf = dnew<unsigned char>(g, N);
+    // an allocator callback may hand out blocks without 16-byte alignment:
+    // the staging copies then fall back to plain loads
+    auto al16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    D.al16 = al16(D.head) && al16(D.r) && al16(D.rr);
     if (!row || !head || !rev || !aoe || !D.cap || !D.r || !D.rr || !D.h || !D.e || !D.cap_edge || !D.stamp ||
         !D.qb0 || !D.qb1 || !D.wl || !D.cb || !D.ctl || !g->side_buf || !D.hl || !D.hmode || !D.hkey ||
         !D.hrem || !D.hnit || !D.hdone || !D.hcl || !D.hlv0 || !D.hlv1 || !D.hikey || !D.hl2 || !D.hri || !D.astamp || !D.rstamp || !D.rl)
@@ -2978,8 +3190,9 @@ int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const in
         D.err = cudaGetSymbolAddress(reinterpret_cast<void **>(&D.base), g_noalloc_scratch);
         int per_sm = 0, sms = 0;
         if (D.err == cudaSuccess) D.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (D.err == cudaSuccess) D.err = solve_kernels_prepare(dev);
         if (D.err == cudaSuccess)
-            D.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<false>, kBlock, 0);
+            D.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<false>, kBlock, kDynSmem);
         D.grid = std::min(per_sm * sms, kNoAllocMaxGrid);
         if (D.err == cudaSuccess && D.grid < 1) D.err = cudaErrorInvalidConfiguration;
     });
@@ -2995,6 +3208,7 @@ int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const in
     D.cap = const_cast<int *>(cap);      // read only by a solve from zero flow
     D.r = r; D.e = reinterpret_cast<long long *>(excess); D.h = height;
     D.cap_edge = nullptr; D.stamp = nullptr;
+    D.al16 = ((reinterpret_cast<uintptr_t>(head) | reinterpret_cast<uintptr_t>(r)) & 15u) == 0;
     D.ctl = reinterpret_cast<Ctl *>(b + Lo::ctl);
     D.rr = reinterpret_cast<int *>(b + Lo::rr);
     D.qb0 = reinterpret_cast<int *>(b + Lo::qb0);
@@ -3029,7 +3243,8 @@ int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const in
     j.max_iters = 4LL * n + 1000;
     j.time_limit_ns = 60ull * 1000ull * 1000ull * 1000ull;
     void *args[] = {&D, &j};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_solve<false>, dim3(ND.grid), dim3(kBlock), args, 0, st);
+    cudaError_t e =
+        cudaLaunchCooperativeKernel((const void *)k_solve<false>, dim3(ND.grid), dim3(kBlock), args, kDynSmem, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_err(MF_ECUDA, std::string("cooperative launch: ") + cudaGetErrorString(e));

@@ -235,6 +235,54 @@ def test_certificate_catches_planted_mistakes():
     assert "STRUCT" in _cert(g, bad, side, f)[2]
 
 
+def _hand_state(n, tails, heads, caps, s, t, flow_on_edge):
+    """A state written out by hand: one arc pair per input edge (tail -> head
+    listed first), the given flow on each edge, residuals and excesses derived
+    from it (excess = inflow - outflow)."""
+    g = gen.from_edges(n, tails, heads, caps, s, t)
+    out = [[] for _ in range(n)]
+    for i, (u, v, c, f) in enumerate(zip(tails, heads, caps, flow_on_edge)):
+        out[u].append((v, c - f, c, 2 * i))       # forward arc: residual c - f
+        out[v].append((u, f, 0, 2 * i + 1))       # reverse arc: residual f
+    arc_row = np.zeros(n + 1, np.int64)
+    head, r, capa, key = [], [], [], []
+    for u in range(n):
+        for v, res, c, k in out[u]:
+            head.append(v); r.append(res); capa.append(c); key.append(k)
+        arc_row[u + 1] = len(head)
+    pos = {k: a for a, k in enumerate(key)}
+    rev = np.array([pos[k ^ 1] for k in key], np.int64)
+    ex = np.zeros(n, np.int64)
+    for u, v, f in zip(tails, heads, flow_on_edge):
+        ex[v] += f
+        ex[u] -= f
+    st = oracle.OracleState(arc_row=arc_row, head=np.array(head, np.int32), rev=rev,
+                            cap=np.array(capa, np.int64), r=np.array(r, np.int64), excess=ex,
+                            height=np.zeros(n, np.int32))
+    return g, st
+
+
+def test_certificate_signs_bit_alone():
+    """States whose only defect is the sign condition: every other bit holds
+    (residual pairs, excess = net inflow with sum 0, no residual arc from S to
+    T, value = sum over T of the excess = capacity of the cut)."""
+    # a deficit on the source side: s -> a (5), a -> t (1) carrying flow 0 and
+    # 1; S = {s, a}: e(a) = -1, e(t) = 1 = C(S, T)
+    g, st = _hand_state(3, [0, 1], [1, 2], [5, 1], 0, 2, [0, 1])
+    side = np.array([1, 1, 0], np.uint8)
+    bits, _, names = _cert(g, st, side, 1)
+    assert names == ["SIGNS"], names
+    # an excess on the sink side: s -> a (1), a -> t (5) carrying flow 1 and
+    # 0; S = {s}: e(a) = 1 sits in T, sum over T = 1 = C(S, T)
+    g, st = _hand_state(3, [0, 1], [1, 2], [1, 5], 0, 2, [1, 0])
+    side = np.array([1, 0, 0], np.uint8)
+    bits, _, names = _cert(g, st, side, 1)
+    assert names == ["SIGNS"], names
+    # the same graphs with the flow completed are certified
+    g, st = _hand_state(3, [0, 1], [1, 2], [5, 1], 0, 2, [1, 1])
+    assert _cert(g, st, np.array([1, 1, 0], np.uint8), 1)[0] == 0
+
+
 def test_bfs_heights_vs_scipy():
     rng = np.random.default_rng(5)
     g = gen.random_graph(n=300, m=1500, seed=9)
