@@ -300,7 +300,7 @@ void mf_destroy(mf_graph *g);
  * another framework which owns all device memory through its own pool, or a
  * service path where allocations are forbidden after start-up -- and so
  * cannot use mf_create.  Instead of allocating, it works in one static
- * device array of 13,239,040 bytes (about 12.6 MiB) that every GPU which
+ * device array of 14,288,384 bytes (about 13.6 MiB) that every GPU which
  * loads this library holds until the process exits.
  *   n, arcs        vertices (2 .. 131072) and Bi-CSR arcs (0 .. 2097152);
  *                  larger graphs are rejected with MF_EINVAL

@@ -137,6 +137,15 @@ struct Ctl {
     long long solo_seen;  // frontier arcs counted up to that level
     long long st[S_COUNT_MAX];  // statistics, see enum Stat
     long long st_aux[S_COUNT_MAX];  // where a JOB_REFRESH counts, keeping st intact
+    // the activation queue of a PushRelabel phase (see k_solve): consumer
+    // tickets, producer reservations and finished entries, each on its own
+    // 128-byte line (every warp of the grid polls or bumps them)
+    alignas(128) int aq_head;   // (z)
+    alignas(128) int aq_tail;   // (z)
+    alignas(128) int aq_done;   // (z)
+    alignas(128) int aq_over;   // (z) an active vertex was left out (generation cap, full queue)
+    int aq_maxgen;              // (z) highest generation enqueued
+    alignas(128) int aq_fin;    // (z) every queued entry has been processed
 };
 
 enum Stat {
@@ -183,6 +192,8 @@ struct DevGraph {
     unsigned char *part;      // push-pull partition per vertex (kPartT / kPartS / kPartP), or null
     Ctl *ctl;
     int al16;                 // head, r and rr start on 16-byte boundaries (16-byte staging copies)
+    unsigned long long *aq;   // activation queue slots (generation << 32 | vertex + 1; 0 = empty)
+    int qc;                   // its capacity
 };
 
 // Push-pull partitions (Alg. 8): T can reach a sink, S cannot (the previous
@@ -227,10 +238,36 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
+__device__ __forceinline__ int ld_acquire_s32(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// A value every lane of the warp must agree on (it steers warp-wide control
+// flow): read once by lane 0 and broadcast.  A word that other warps write
+// concurrently could otherwise reach the lanes as different values.
+__device__ __forceinline__ int bcast_ld(const int *p) {
+    return __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 ? __ldcg(p) : 0, 0);
+}
+__device__ __forceinline__ long long bcast_ld(const long long *p) {
+    return __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 ? __ldcg(p) : 0ll, 0);
 }
 
 __device__ __forceinline__ long long warp_sum(long long v) {
@@ -376,6 +413,7 @@ struct Front {
     int *stage;     // this warp's kWq shared ints, or nullptr
     int sn;         // staged entries (warp-uniform)
     long long ds;   // arc total not yet added (warp-uniform)
+    unsigned mark;  // activation stamp given to the worklist entries (queued from the start)
 };
 
 // Publish the staged entries and do their bookkeeping: each joins the global
@@ -415,6 +453,7 @@ __device__ __forceinline__ void front_flush_entries(const DevGraph &G, Front &F,
             K.bfs_verts += ok[j];
             hub[j] = act && deg[j] > kHubDeg;
             small[j] = act && !hub[j];
+            if (small[j]) G.astamp[v[j]] = F.mark;
         }
         warp_append_n(small, v, &G.ctl->wcnt, G.wl);
         warp_append_n(hub, v, &G.ctl->hcnt, G.hl);
@@ -487,6 +526,7 @@ __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (
         const bool act = disc[j] && (((fwd >> j) & 1u) ? ev[j] < 0 : ev[j] > 0);
         hub[j] = act && deg[j] > kHubDeg;
         small[j] = act && !hub[j];
+        if (small[j]) G.astamp[v[j]] = F.mark;
     }
     ds = warp_sum(ds);
     if ((threadIdx.x & 31) == 0 && ds) add_ll(F.asum, ds);
@@ -649,11 +689,11 @@ __device__ __forceinline__ void bfs_bottom_up_item(const DevGraph &G, int2 item,
     const int v = item.x;
     const int side = dual ? G.part[v] : kPartT;
     bool disc = false;
-    if (lcg(&G.h[v]) == G.n) {
+    if (bcast_ld(&G.h[v]) == G.n) {
         const int a1 = min(item.y + kChunk, __ldg(&G.row[v + 1]));
         bool hit = false;
         for (int a0 = item.y; a0 < a1 && !hit; a0 += 32 * kIlpB) {
-            if (a0 != item.y && __shfl_sync(kFull, lane == 0 ? lcg(&G.h[v]) : 0, 0) != G.n) break;
+            if (a0 != item.y && bcast_ld(&G.h[v]) != G.n) break;
             ArcRoundBfs R;
 #pragma unroll
             for (int j = 0; j < kIlpB; ++j) {
@@ -720,7 +760,53 @@ struct ActList {
     int *hcnt;         // the next pass's hub list (high-degree vertices a push
     int *hlist;        //   turned active), its size and its stamp
     unsigned hstamp;
+    // queue mode (the PushRelabel phases of the data-driven and push-pull
+    // modes): activated vertices go to the activation queue with generation
+    // gen instead of to list; stamp then marks "queued or being processed"
+    unsigned long long *aq;   // or nullptr: round lists
+    int qc, gen, gen_cap;
+    Ctl *C;
 };
+
+// Enqueue the lanes' flagged vertices of N slots into the activation queue
+// with generation AL.gen (one reservation per warp); entries past the queue's
+// capacity are dropped, counted as finished and flagged (the iteration then
+// ends on another global relabel).  All 32 lanes call.
+template <int N>
+__device__ __forceinline__ void aq_push_n(const ActList &AL, const bool (&pred)[N], const int (&val)[N]) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    unsigned m[N];
+    int tot = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        m[j] = __ballot_sync(kFull, pred[j]);
+        tot += __popc(m[j]);
+    }
+    if (tot == 0) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&AL.C->aq_tail, tot);
+    base = __shfl_sync(kFull, base, 0);
+    int over = 0;
+    const unsigned long long tag = (unsigned long long)(unsigned)AL.gen << 32;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        if (pred[j]) {
+            const int pos = base + __popc(m[j] & below);
+            if (pos < AL.qc) st_release_u64(&AL.aq[pos], tag | (unsigned)(val[j] + 1));
+            else ++over;
+        }
+        base += __popc(m[j]);
+    }
+    over = (int)warp_sum((long long)over);
+    if (lane == 0) {
+        atomicMax(&AL.C->aq_maxgen, AL.gen);
+        if (over) {
+            atomicAdd(&AL.C->aq_done, over);
+            atomicExch(&AL.C->aq_over, 1);
+        }
+    }
+}
 
 // A vertex whose height PushRelabel raised joins the relabel list of the loop
 // iteration once: only relabelled vertices can own arcs that RemoveInvalidEdges
@@ -728,6 +814,58 @@ struct ActList {
 // make steep).  One thread calls.
 __device__ __forceinline__ void note_relabel(const DevGraph &G, int u, unsigned rstamp) {
     if (atomicExch(&G.rstamp[u], rstamp) != rstamp) G.rl[atomicAdd(&G.ctl->rlcnt, 1)] = u;
+}
+
+// Single-thread enqueue of v (as aq_push_n).
+__device__ __forceinline__ void aq_push_one(const ActList &AL, int v) {
+    const int pos = atomicAdd(&AL.C->aq_tail, 1);
+    if (pos < AL.qc) {
+        st_release_u64(&AL.aq[pos], ((unsigned long long)(unsigned)AL.gen << 32) | (unsigned)(v + 1));
+    } else {
+        atomicAdd(&AL.C->aq_done, 1);
+        atomicExch(&AL.C->aq_over, 1);
+    }
+    atomicMax(&AL.C->aq_maxgen, AL.gen);
+}
+
+// File the vertices that moves turned active (add: worklist vertices, degree
+// <= kHubDeg; add_hub: hubs; neither s nor t): each joins the next activation
+// round's list -- in queue mode the activation queue -- or the next pass's
+// hub list, once, by the list's stamp.  In queue mode a vertex is marked
+// from its enqueue until the warp that processes it has finished, and that
+// warp clears the mark before it reads the vertex's excess a last time: with
+// a fence between the excess atomic and the mark here, and between the clear
+// and the read there, at least one side sees the other, so a vertex that a
+// push turns active while it is being processed is queued again exactly once
+// and no activation is lost.  Past the generation cap a vertex is left
+// active, unqueued, and the phase is flagged.  All 32 lanes call.
+template <int N>
+__device__ __forceinline__ void file_activations(const DevGraph &G, bool (&add)[N], bool (&add_hub)[N],
+                                                 const int (&v)[N], const ActList &AL) {
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < N; ++j) any |= add[j] || add_hub[j];
+    if (!__any_sync(kFull, any)) return;
+    if (AL.aq) {
+        if (AL.gen >= AL.gen_cap) {
+            bool capped = false;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                capped |= add[j];
+                add[j] = false;
+            }
+            if (__any_sync(kFull, capped) && (threadIdx.x & 31) == 0) atomicExch(&AL.C->aq_over, 1);
+        }
+        __threadfence();
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        if (add[j]) add[j] = atomicExch(&G.astamp[v[j]], AL.stamp) != AL.stamp;
+        if (add_hub[j]) add_hub[j] = atomicExch(&G.astamp[v[j]], AL.hstamp) != AL.hstamp;
+    }
+    if (AL.aq) aq_push_n(AL, add, v);
+    else warp_append_n(add, v, AL.cnt, AL.list);
+    warp_append_n(add_hub, v, AL.hcnt, AL.hlist);
 }
 
 // One round of a warp's arc scan: lane i holds arcs a0 + 32 j + i (j < kIlp)
@@ -838,24 +976,14 @@ __device__ __forceinline__ long long move_round(const DevGraph &G, int a0, const
         }
     }
     bool add[kIlp], add_hub[kIlp];
-    bool any = false;
 #pragma unroll
     for (int j = 0; j < kIlp; ++j) {
         const bool turned = PULL ? (old[j] >= 0 && old[j] - d[j] < 0) : (old[j] <= 0 && old[j] + d[j] > 0);
         const bool cand = d[j] > 0 && turned && R.v[j] != G.s && R.v[j] != G.t;
         add[j] = cand && deg[j] <= kHubDeg;
         add_hub[j] = cand && deg[j] > kHubDeg;
-        any |= cand;
     }
-    if (__any_sync(kFull, any)) {
-#pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            if (add[j]) add[j] = atomicExch(&G.astamp[R.v[j]], AL.stamp) != AL.stamp;
-            if (add_hub[j]) add_hub[j] = atomicExch(&G.astamp[R.v[j]], AL.hstamp) != AL.hstamp;
-        }
-        warp_append_n(add, R.v, AL.cnt, AL.list);
-        warp_append_n(add_hub, R.v, AL.hcnt, AL.hlist);
-    }
+    file_activations(G, add, add_hub, R.v, AL);
     return sent;
 }
 
@@ -967,24 +1095,14 @@ __device__ __forceinline__ long long move_batch(const DevGraph &G, const int (&a
         }
     }
     bool add[N], add_hub[N];
-    bool any = false;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         const bool turned = PULL ? (old[j] >= 0 && old[j] - d[j] < 0) : (old[j] <= 0 && old[j] + d[j] > 0);
         const bool cand = d[j] > 0 && turned && v[j] != G.s && v[j] != G.t;
         add[j] = cand && deg[j] <= kHubDeg;
         add_hub[j] = cand && deg[j] > kHubDeg;
-        any |= cand;
     }
-    if (__any_sync(kFull, any)) {
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            if (add[j]) add[j] = atomicExch(&G.astamp[v[j]], AL.stamp) != AL.stamp;
-            if (add_hub[j]) add_hub[j] = atomicExch(&G.astamp[v[j]], AL.hstamp) != AL.hstamp;
-        }
-        warp_append_n(add, v, AL.cnt, AL.list);
-        warp_append_n(add_hub, v, AL.hcnt, AL.hlist);
-    }
+    file_activations(G, add, add_hub, v, AL);
     return sent;
 }
 
@@ -1048,9 +1166,19 @@ template <bool PULL>
 __device__ __forceinline__ void pr_finish_t(const DevGraph &G, int u, int hu, bool relabelled, const ActList &AL) {
     if ((threadIdx.x & 31) == 0) {
         if (relabelled) note_relabel(G, u, AL.rstamp);
+        if (AL.aq) {
+            atomicExch(&G.astamp[u], 0u);   // u leaves the queue before its excess is read (file_activations)
+            __threadfence();
+        }
         const long long eu = lcg(&G.e[u]);
-        if (hu < G.n && (PULL ? eu < 0 : eu > 0) && atomicExch(&G.astamp[u], AL.stamp) != AL.stamp)
-            AL.list[atomicAdd(AL.cnt, 1)] = u;
+        if (hu < G.n && (PULL ? eu < 0 : eu > 0)) {
+            if (AL.aq && AL.gen >= AL.gen_cap) {
+                atomicExch(&AL.C->aq_over, 1);
+            } else if (atomicExch(&G.astamp[u], AL.stamp) != AL.stamp) {
+                if (AL.aq) aq_push_one(AL, u);
+                else AL.list[atomicAdd(AL.cnt, 1)] = u;
+            }
+        }
     }
     __syncwarp();
 }
@@ -1088,10 +1216,10 @@ __device__ __forceinline__ void push_relabel_small_t(const DevGraph &G, int u, i
                                                   const ActList &AL, const unsigned char *pt, unsigned char side,
                                                   Counters &K) {
     const int lane = threadIdx.x & 31;
-    int hu = lcg(&G.h[u]);
+    int hu = bcast_ld(&G.h[u]);
     bool relabelled = false;
     for (int c = 0; c < kc && hu < G.n; ++c) {
-        long long eu = lcg(&G.e[u]);
+        const long long eu = bcast_ld(&G.e[u]);
         ArcRound R;
         load_round_t<PULL, true>(G, beg, end, R, pt, side);
         K.pr_arcs += round_arcs(beg, end);
@@ -1120,10 +1248,10 @@ __device__ __forceinline__ void push_relabel_staged_t(const DevGraph &G, int u, 
     const int lane = threadIdx.x & 31;
     int *sv = stg, *sr = stg + kStgInts, *sh = stg + 2 * kStgInts;
     stage_copy(G.head, sv, beg, end, G.A, G.al16);
-    int hu = lcg(&G.h[u]);
+    int hu = bcast_ld(&G.h[u]);
     bool relabelled = false;
     for (int c = 0; c < kc && hu < G.n; ++c) {
-        const long long eu = lcg(&G.e[u]);
+        const long long eu = bcast_ld(&G.e[u]);
         stage_copy(PULL ? G.rr : G.r, sr, beg, end, G.A, G.al16);
         stage_wait();
         K.pr_arcs += (end - beg + 31 - lane) / 32;
@@ -1227,7 +1355,7 @@ __device__ __forceinline__ long long hub_move_item(const DevGraph &G, int a0, in
         // the hub's excess may already be reserved by the items before this
         // one (not checked in the first push-pull stage, where scanning every
         // item measured faster: its pushes spread over the hub's arcs)
-        if (skip_done && lcg(rem) <= 0) break;
+        if (skip_done && bcast_ld(rem) <= 0) break;
         ArcRound R;
         load_round_t<PULL, true>(G, a0, a1, R, pt, side);
         K.pr_arcs += round_arcs(a0, a1);
@@ -1536,9 +1664,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     unsigned snext = stamp_base;   // next unused activation stamp
     for (it = 0; !fast; ++it) {
         const int par = (int)(it & 1);
+        // the stamp of the first PushRelabel pass's queue: the BFS gives it to
+        // the worklist entries it files (queued from the start)
+        const unsigned wmark0 = snext++;
         // height init: t and deficient vertices are sinks (height 0), all
         // others n; the sinks form BFS level 0.
         if (gtid == 0) {
+            C->aq_head = C->aq_tail = C->aq_done = C->aq_over = C->aq_maxgen = C->aq_fin = 0;
             C->qcnt[1] = 0;
             C->qcnt[2] = 0;
             C->ccnt[0] = 0;
@@ -1636,7 +1768,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     for (;;) {
                         int *ccs = &C->ccnt[Ls % 3];
                         int *spill = (Ls & 1) ? G.qb0 : G.qb1;   // positions >= kSoloCap of the next frontier
-                        Front SF{&s_cnt[b ^ 1], s_front[b ^ 1], &s_arcs[b ^ 1], kSoloCap, spill, nullptr, 0, 0};
+                        Front SF{&s_cnt[b ^ 1], s_front[b ^ 1], &s_arcs[b ^ 1], kSoloCap, spill, nullptr, 0, 0, wmark0};
                         int gs = 32;   // frontier vertices per warp: fewer when they do not fill the warps
                         while (gs > 1 && (gs >> 1) * (kBlock / 32) >= cs) gs >>= 1;
                         for (int grp = cw; grp * gs < cs; grp += kBlock / 32) {
@@ -1724,7 +1856,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 C->asum[(L + 2) % 3] = 0;
                 if (bottom_up) ST[S_BU_LEVELS] += 1;
             }
-            Front FR{ncnt, NF, asum, 0x7fffffff, nullptr, s_bfs + (threadIdx.x >> 5) * kWq, 0, 0};
+            Front FR{ncnt, NF, asum, 0x7fffffff, nullptr, s_bfs + (threadIdx.x >> 5) * kWq, 0, 0, wmark0};
             if (bottom_up) {
                 // groups of 32 consecutive vertex ids (warp w: groups w, w + W, ...)
                 const int groups = (n + 31) / 32;
@@ -1835,7 +1967,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         for (int pass = 0; pass < (PP ? kMaxPassesPP : kMaxPasses); ++pass) {
             const int *HL = (pass & 1) ? G.hl2 : G.hl;
             const int nhp = pass == 0 ? nh : pend;
-            const unsigned wstamp = snext++;   // this pass's round-0 list
+            const unsigned wstamp = pass == 0 ? wmark0 : snext++;   // this pass's round-0 list / queue
             const unsigned hstamp = snext++;   // the next pass's hub list
             int *const pcnt = &C->phc[(pass + 1) & 1];
             // pass 0 appends to phc[1] and starts its rounds on the counters
@@ -1852,7 +1984,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 C->hlc[0] = C->hlc[1] = 0;
                 ST[S_WL] += nhp;
             }
-            const ActList AL0{&C->wcnt, G.wl, wstamp, rstamp_it, pcnt, (pass & 1) ? G.hl : G.hl2, hstamp};
+            // the data-driven and push-pull modes run PushRelabel from the
+            // activation queue; the topology-driven mode in rounds
+            const bool qmode = J.mode != MF_MODE_TOPOLOGY && G.aq != nullptr;
+            const ActList AL0{&C->wcnt, G.wl,   wstamp,     rstamp_it, pcnt, (pass & 1) ? G.hl : G.hl2,
+                              hstamp,   qmode ? G.aq : nullptr, G.qc, 0, max_rounds, C};
             bool pass_hubs_clean = true;
             if (nhp > 0) {
                 pass_hubs_clean = false;
@@ -1882,6 +2018,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     for (int c = lane; c < nc; c += 32) G.hcl[pos + c] = make_int2(i, beg + c * kPrChunk);
                 }
                 MF_SYNC_T(S_T_HUB, -1, 0, nhp);
+                // a later pass's queue: the previous pass's counters have been
+                // read (before this barrier), and nothing is queued before the
+                // first H3 (a later pass's first cycle has an H1 barrier)
+                if (pass > 0 && gtid == 0)
+                    C->aq_head = C->aq_tail = C->aq_done = C->aq_over = C->aq_maxgen = C->aq_fin = 0;
                 const int nhc = lcg(&C->hccnt);
                 const int hub_cycles = kc > kMinHubCycles ? kc : kMinHubCycles;
                 for (int c = 0; c < hub_cycles; ++c) {
@@ -2048,7 +2189,80 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             }
             bool pass_rounds_clean = true;
             int cnt = lcg(&C->wcnt);
-            if (cnt > 0 || (pass == 0 && J.mode == MF_MODE_TOPOLOGY)) {
+            const int qtail0 = qmode ? lcg(&C->aq_tail) : 0;   // queued by the hub cycles
+            if (qmode && cnt + qtail0 > 0) {
+                // PushRelabel from the activation queue, without rounds: the
+                // worklist entries (generation 0) are dealt to the warps by
+                // stride, then each warp takes a ticket for the next queued
+                // entry and waits for it; a vertex that a push turns active is
+                // queued at once with the next generation and taken by the next
+                // free warp, so a slow vertex holds up only the vertices it
+                // activates.  The phase ends when every queued entry has been
+                // processed (the warp whose completion makes the count of
+                // processed entries equal to the count of queued ones raises
+                // aq_fin).  Generations stand for the activation rounds: none
+                // past max_rounds is queued.  One grid barrier at the end.
+                const int n0 = cnt;
+                for (int i = gwarp;; i += nwarps) {
+                    int u = -1, gen = 0;
+                    if (i < n0) {
+                        u = lcg(&G.wl[i]);
+                    } else {
+                        int q = 0;
+                        unsigned long long slot = 0;
+                        if (lane == 0) {
+                            q = atomicAdd(&C->aq_head, 1);
+                            const unsigned long long t0 = gtimer();
+                            unsigned ns = 32;
+                            for (int k = 0;; ++k) {
+                                if (q < G.qc) {
+                                    slot = ld_acquire_u64(&G.aq[q]);
+                                    if (slot) {
+                                        G.aq[q] = 0;   // the slot is free again for the next phase
+                                        break;
+                                    }
+                                }
+                                if ((k & 3) == 3 && ld_acquire_s32(&C->aq_fin)) break;
+                                if (gtimer() - t0 > kWaitNs) {
+                                    atomicOr(&C->status, ST_WAIT);
+                                    break;
+                                }
+                                __nanosleep(ns);
+                                ns = ns < 1024 ? 2 * ns : ns;
+                            }
+                        }
+                        slot = __shfl_sync(kFull, slot, 0);
+                        if (!slot) break;   // every entry processed (or a wait gave up)
+                        u = (int)(slot & 0xffffffffu) - 1;
+                        gen = (int)(slot >> 32);
+                    }
+                    const ActList AL{nullptr, nullptr, wstamp, rstamp_it, pcnt, AL0.hlist, hstamp,
+                                     G.aq,    G.qc,    gen + 1, max_rounds, C};
+                    if (stage == 1) {
+                        const unsigned char side = G.part[u];
+                        if (side == kPartS)
+                            push_relabel_warp_t<true>(G, u, kc, AL, G.part, side, stg, K);
+                        else
+                            push_relabel_warp_t<false>(G, u, kc, AL, G.part, side, stg, K);
+                    } else {
+                        push_relabel_warp(G, u, kc, AL, stg, K);
+                    }
+                    if (lane == 0) {
+                        // this entry's own enqueues, and (by the acquire) those
+                        // of every entry counted before it, precede the tail read
+                        const int d = arrive_acq_rel(&C->aq_done) + 1;
+                        if (d == n0 + ld_acquire_s32(&C->aq_tail)) atomicExch(&C->aq_fin, 1);
+                    }
+                }
+                MF_SYNC_T(S_T_PRW, 0, 0, cnt + lcg(&C->aq_tail));
+                pass_rounds_clean = lcg(&C->aq_over) == 0;
+                if (gtid == 0) {
+                    ST[S_ROUNDS] += lcg(&C->aq_maxgen) + 1;
+                    ST[S_WL] += cnt + lcg(&C->aq_tail);
+                }
+                // (the counters are zeroed for the next pass after its set-up
+                // barrier, when every thread has read them)
+            } else if (!qmode && (cnt > 0 || (pass == 0 && J.mode == MF_MODE_TOPOLOGY))) {
                 pass_rounds_clean = false;
                 const int *list = G.wl;
                 for (int rd = 0;; ++rd) {
@@ -2124,7 +2338,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         for (int w = gwarp; w < nri; w += nwarps) {
             const int2 item = lcg(&G.hri[w]);
             const int u = item.x;
-            const int hu = lcg(&G.h[u]);
+            const int hu = bcast_ld(&G.h[u]);
             const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
             const unsigned char side = stage == 1 ? G.part[u] : (stage == 2 ? kPartP : kPartT);
             if (PP && side == kPartS) {
@@ -2393,10 +2607,11 @@ struct NoAllocLayout {
     static constexpr size_t hrem = hkey + align256(sizeof(unsigned long long) * kNoAllocMaxHubs);
     static constexpr size_t hl2 = hrem + align256(sizeof(long long) * kNoAllocMaxHubs);
     static constexpr size_t hri = hl2 + align256(sizeof(int) * kNoAllocMaxHubs);
-    static constexpr size_t total = hri + align256(sizeof(int2) * (kNoAllocMaxArcs / kPrChunk + kNoAllocMaxHubs));
+    static constexpr size_t aq = hri + align256(sizeof(int2) * (kNoAllocMaxArcs / kPrChunk + kNoAllocMaxHubs));
+    static constexpr size_t total = aq + align256(sizeof(unsigned long long) * kNoAllocMaxN);
 };
 
-static_assert(NoAllocLayout::total == 13239040, "the header states the scratch size (13,239,040 bytes)");
+static_assert(NoAllocLayout::total == 14288384, "the header states the scratch size (14,288,384 bytes)");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NoAllocLayout::total];
 
 }  // namespace mf
@@ -2753,6 +2968,8 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     D.rstamp = dnew<unsigned>(g, N);
     D.rl = dnew<int>(g, N);
     D.part = g->opt.mode == MF_MODE_PUSH_PULL ? dnew<unsigned char>(g, N) : nullptr;
+    D.qc = int(std::max<size_t>(N, 1024));
+    D.aq = dnew<unsigned long long>(g, size_t(D.qc));
     D.ctl = dnew<Ctl>(g, 1);
     g->side_buf = dnew<unsigned char>(g, N);
     // an allocator callback may hand out blocks without 16-byte alignment:
@@ -2761,7 +2978,8 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     D.al16 = al16(D.head) && al16(D.r) && al16(D.rr);
     if (!row || !head || !rev || !aoe || !D.cap || !D.r || !D.rr || !D.h || !D.e || !D.cap_edge || !D.stamp ||
         !D.qb0 || !D.qb1 || !D.wl || !D.cb || !D.ctl || !g->side_buf || !D.hl || !D.hmode || !D.hkey ||
-        !D.hrem || !D.hnit || !D.hdone || !D.hcl || !D.hlv0 || !D.hlv1 || !D.hikey || !D.hl2 || !D.hri || !D.astamp || !D.rstamp || !D.rl)
+        !D.hrem || !D.hnit || !D.hdone || !D.hcl || !D.hlv0 || !D.hlv1 || !D.hikey || !D.hl2 || !D.hri || !D.astamp ||
+        !D.rstamp || !D.rl || !D.aq)
         return fail(MF_ENOMEM, "device allocation failed");
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
@@ -2771,6 +2989,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
         up(rev, H.rev.data(), size_t(H.arcs) * 4) || up(aoe, H.arc_of_edge.data(), size_t(m) * 4) ||
         up(D.cap, H.cap.data(), size_t(H.arcs) * 4) || up(D.cap_edge, cap_edge.data(), size_t(m) * 4) ||
         cudaMemsetAsync(D.stamp, 0, M * 4, st) || cudaMemsetAsync(D.ctl, 0, sizeof(Ctl), st) ||
+        cudaMemsetAsync(D.aq, 0, size_t(D.qc) * 8, st) ||
         cudaMemsetAsync(D.e, 0, N * 8, st) || cudaMemsetAsync(D.h, 0, N * 4, st) ||
         cudaMemsetAsync(D.astamp, 0, N * 4, st) || cudaMemsetAsync(D.rstamp, 0, N * 4, st) ||
         cudaMemsetAsync(D.r, 0, A * 4, st) || cudaMemsetAsync(D.rr, 0, A * 4, st) ||
@@ -2805,6 +3024,8 @@ int mf_solve(mf_graph *g, void *stream) {
     MF_CUDA(cudaMemsetAsync(g->dg.stamp, 0, size_t(std::max<int64_t>(g->m, 1)) * 4, st));
     MF_CUDA(cudaMemsetAsync(g->dg.astamp, 0, size_t(g->n) * 4, st));
     MF_CUDA(cudaMemsetAsync(g->dg.rstamp, 0, size_t(g->n) * 4, st));
+    // a launch that gave up inside a PushRelabel phase may have left queue entries
+    MF_CUDA(cudaMemsetAsync(g->dg.aq, 0, size_t(g->dg.qc) * 8, st));
     Job j{};
     j.kind = JOB_SOLVE;
     j.kc = g->kc;
@@ -3230,8 +3451,11 @@ int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const in
     D.hrem = reinterpret_cast<long long *>(b + Lo::hrem);
     D.hl2 = reinterpret_cast<int *>(b + Lo::hl2);
     D.hri = reinterpret_cast<int2 *>(b + Lo::hri);
+    D.aq = reinterpret_cast<unsigned long long *>(b + Lo::aq);
+    D.qc = std::min(std::max(n, 1024), kNoAllocMaxN);
     // the previous call's contents stay in the array: clear what must start at 0
     MF_CUDA(cudaMemsetAsync(D.ctl, 0, sizeof(Ctl), st));
+    MF_CUDA(cudaMemsetAsync(D.aq, 0, sizeof(unsigned long long) * size_t(D.qc), st));
     MF_CUDA(cudaMemsetAsync(D.astamp, 0, sizeof(unsigned) * size_t(n), st));
     MF_CUDA(cudaMemsetAsync(D.rstamp, 0, sizeof(unsigned) * size_t(n), st));
     Job j{};
