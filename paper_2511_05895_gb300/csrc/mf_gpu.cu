@@ -538,9 +538,13 @@ __device__ __forceinline__ void bfs_discovered_n(const DevGraph &G, const bool (
 // lane: as bfs_discovered_n.  All 32 lanes call.
 __device__ __forceinline__ void bfs_discovered(const DevGraph &G, bool disc, int v, bool fwd, bool dual,
                                                Front &F, Counters &K) {
-    const bool d1[kIlpB] = {disc, false, false, false};
-    const int v1[kIlpB] = {v, 0, 0, 0};
-    static_assert(kIlpB == 4, "single-slot form of bfs_discovered_n");
+    bool d1[kIlpB];
+    int v1[kIlpB];
+#pragma unroll
+    for (int j = 0; j < kIlpB; ++j) {
+        d1[j] = j == 0 && disc;
+        v1[j] = j == 0 ? v : 0;
+    }
     bfs_discovered_n(G, d1, v1, fwd ? 1u : 0u, dual, F, K);
 }
 
