@@ -56,21 +56,22 @@ UNIT = "batches/s"
 SCALE = 20
 SEED = 1
 
-# Algorithmic bytes per unit of work of the repair kernel (the design doc lists the
-# same figures with their derivation).
+# Algorithmic bytes per unit of work of the repair kernel: the per-unit
+# figures of the method's memory accesses, each random 4-byte gather counted
+# as 4 bytes and an atomic read-modify-write as its operand size.
 BYTES = {
     "bfs_arcs": 12,       # head 4 + mirrored residual 4 + height of the head 4
-    "bfs_vertices": 20,   # row offsets 8 + height write 4 + queue write 4 + queue read 4
+    "bfs_vertices": 12,   # row offsets 8 + height write 4
     "height_init": 12,    # per vertex per BFS: excess 8 + height write 4 (+ 8 per vertex for
                           # the deficit recount of a loop that ends without a final BFS)
-    "pr_arcs": 12,        # residual 4 + head 4 + height of the head 4
-    "pushes": 64,         # 4 int32 residual RMW (8 each) + 2 int64 excess RMW (16 each)
+    "pr_arcs": 12,        # residual 4 + head 4 + height of the head 4 (one scan per step)
+    "pushes": 28,         # residual 4 + reverse residual 4 + reverse arc 4 + excess of u 8 + of v 8
     "relabels": 4,
     "ri_arcs": 12,
-    "ri_moves": 64,
+    "ri_moves": 28,
     "worklist": 8,        # worklist write + read
-    "batch": 64,          # id+cap 8, cap_edge RMW 8, arc map 4, stamp RMW 8, cap/r/rr RMW 24, scratch 12
-    "clamped": 48,
+    "batch": 32,          # id + cap 8, cap_edge 4, arc map 4, residual RMW 8, arc capacity RMW 8
+    "clamped": 24,        # reverse residual 4 + reverse arc 4 + two int64 excesses 16
     "resat_arcs": 4,
 }
 
@@ -99,7 +100,8 @@ def kernel_source_hash() -> str:
 
 def recorded_traffic(kernel_hash: str):
     """DRAM bytes per launch of k_solve from the committed ncu summary, if it
-    was taken on this exact kernel source; else None."""
+    was taken on this exact kernel source (recorded by an earlier capture, not
+    measured in this run); else None."""
     p = os.path.join(ROOT, "profiles", "k_solve_rmat20_batch100k.md")
     if not os.path.exists(p):
         return None
@@ -212,7 +214,8 @@ def serving_measurement(rates, duration_s: float, seed: int = 5) -> dict:
     a rectangle of that many terminal arcs), served by mf_server with per-graph
     grids of 19 to 152 CTAs, every graph repaired by Dynamic Push-Pull.  Reports
     p50/p99 submit-to-completion latency and the completed batches per second
-    at each rate."""
+    at each rate.  Each request's repair runs on a grid sized to its batch
+    (the graph's full grid, half or a quarter; see mf_server)."""
     from concurrent.futures import ThreadPoolExecutor
     from paper_2511_05895_gb300 import MF_MODE_PUSH_PULL, MaxFlowGraph, Server
     makers = [(lambda: gen.rmat(scale=16, seed=301), 19), (lambda: gen.rmat(scale=18, seed=302), 38),
@@ -268,6 +271,7 @@ def serving_measurement(rates, duration_s: float, seed: int = 5) -> dict:
                      "batches_per_s": round(st["completed"] / max(st["makespan_s"], 1e-9), 1),
                      "p50_ms": round(st["p50_us"] / 1000, 3), "p99_ms": round(st["p99_us"] / 1000, 3),
                      "max_inflight": st["max_inflight"], "captured_graphs": st["captured_graphs"],
+                     "replays": st["replays"], "direct_launches": st["direct_launches"],
                      "failed": st["failed"]})
     # every graph's final value against a fresh static solve of its final capacities
     exact = True
@@ -379,11 +383,31 @@ def grid_measurement(batches: int, flush, peak: float, seed: int = 3) -> dict:
                         "rewriting terminal capacities", "batches": batches,
             "entries_median": int(statistics.median(ks)), "dynamic_ms": round(d, 3),
             "push_pull_ms": round(pm, 3), "static_recompute_ms": round(s_, 3), "speedup": round(s_ / d, 3),
-            "push_pull_speedup": round(s_ / pm, 3),
+            "push_pull_speedup": round(s_ / pm, 3), "dynamic_spread_ms": spread(dyn),
+            "push_pull_spread_ms": spread(ppt), "static_spread_ms": spread(sta),
             "hbm_frac_of_measured": round(statistics.median(fr), 4), "values_equal": equal}
 
 
 MODES = {"data-driven": 0, "topology": 1, "push-pull": 2}
+
+
+def certify_state(G, g, cap, flow) -> bool:
+    """The optimality certificate of the GPU state (capacity feasibility,
+    excess bookkeeping, a cut with no residual arc from S to T, signs, value =
+    cut capacity, heights = BFS fixed point), checked by the oracle's C
+    checker on the host."""
+    import oracle
+    st = G.export_graph()
+    r, e, h = G.export_state()
+    side = G.min_cut()
+    bits, _, _ = oracle.certify(g.n, g.row_ptr, g.col, cap, g.s, g.t, st["arc_row"], st["head"],
+                                st["rev"].astype(np.int64), st["cap"], r, e, side, flow, h)
+    return bits == 0
+
+
+def spread(xs) -> dict:
+    """min / median / max of a sample (ms)."""
+    return {"min": round(min(xs), 4), "median": round(statistics.median(xs), 4), "max": round(max(xs), 4)}
 
 
 def time_repairs(G, dev, warmup, flush, stream):
@@ -450,6 +474,7 @@ def cpu_oracle_sample(g, args) -> dict:
             wall = time.perf_counter() - t0
     per = [sec for _, sec in res]
     return {"value": len(jobs) / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "flows": [f for f, _ in res],
             "seconds_per_batch_one_core": round(statistics.mean(per), 3),
             "sample": f"{len(jobs)} recomputes from scratch (FIFO push-relabel, one thread each) of the "
                       f"RMAT-20 graph after {args.batch}-edge batches, as {cores} parallel processes "
@@ -460,7 +485,8 @@ def workload_config(args, g) -> dict:
     return {"workload": f"RMAT scale {SCALE} (n={g.n}, m={g.m}, a=0.57 b=0.19 c=0.19), caps U[1,1000], "
                         f"mixed batches of {args.batch} edges (+/-U[1,500])",
             "n": g.n, "m": g.m, "batch_edges": args.batch, "seed": SEED,
-            "kernel_cycles": args.kc, "policy": args.policy, "mode": args.mode,
+            "kernel_cycles": args.kc, "policy": args.policy,
+            "mode": "chosen per batch by the learned policy" if args.policy == "learned" else args.mode,
             "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -480,8 +506,11 @@ def main():
     ap.add_argument("--policy", default="fixed", choices=["fixed", "plain", "learned"],
                     help="batch policy: fixed repair, the plain rule, or the trained network")
     ap.add_argument("--mode", default="data-driven", choices=list(MODES),
-                    help="processing mode of the timed repairs (Sec. 5.2 / 5.3 / Alg. 8)")
+                    help="processing mode of the timed repairs (Sec. 5.2 / 5.3 / Alg. 8); with --policy learned "
+                         "the network chooses it per batch")
     ap.add_argument("--no-pp", action="store_true", help="skip the Dynamic Push-Pull comparison")
+    ap.add_argument("--size-batches", type=int, default=20, help="batches per size in the dynamic/static sweep")
+    ap.add_argument("--grid-batches", type=int, default=20, help="rectangle batches on the 4096^2 grid")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -506,7 +535,10 @@ def main():
 
     g = gen.rmat(scale=SCALE, seed=SEED + 1000 * rank)
     cap = g.cap.copy()
-    G = MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t, kernel_cycles=args.kc, mode=MODES[args.mode])
+    # the learned policy picks the processing mode per batch: the graph keeps
+    # the push-pull state (and the exact cut) so that all three are open
+    gmode = MODES["push-pull"] if args.policy == "learned" else MODES[args.mode]
+    G = MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t, kernel_cycles=args.kc, mode=gmode)
     G.solve()
     flow0 = G.flow_value()
     if args.policy != "fixed":
@@ -532,8 +564,11 @@ def main():
         e1.record(stream)
         return e0, e1
 
+    flows = []   # the GPU's value after each batch (warm-up and timed), read outside the timing
     for i in range(args.warmup):
-        timed_step(*dev[i])
+        a, b = timed_step(*dev[i])
+        b.synchronize()
+        flows.append(G.flow_value())
     G.sync()
     stats_acc = {k: 0 for k in [b for b in BYTES if b != "height_init"] +
                  ["iterations", "bfs_levels", "t_batch_ns", "t_reset_ns", "t_bfs_ns", "t_pr_ns",
@@ -544,16 +579,18 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    events, per_step_bytes = [], []
+    events, per_step_bytes, chosen = [], [], []
     for i in range(args.warmup, args.warmup + args.steps):
         ev = timed_step(*dev[i])
         events.append(ev)
         # device counters of this launch (read after it completes; outside the timing)
         ev[1].synchronize()
         st = G.stats()
+        flows.append(G.flow_value())
         per_step_bytes.append(algorithmic_bytes(st, g.n))
         for k in stats_acc:
             stats_acc[k] += st[k] if k != "clean_exits" else int(st["exit_kind"] == 1)
+        chosen.append((st["policy_kind"], st["policy_kernel_cycles"], st["policy_mode"]))
     torch.cuda.synchronize()
     clk = clocks.stop()
     times = [a.elapsed_time(b) for a, b in events]          # ms
@@ -563,14 +600,8 @@ def main():
     G.sync()
     flow_after = G.flow_value()
 
-    # certificate of the final state (optimality proof; no oracle needed)
-    import oracle
-    from tests._helpers import certify_gpu
-    certified = True
-    try:
-        certify_gpu(G, g, host_cap, flow_after)
-    except AssertionError:
-        certified = False
+    # certificate of the final state (optimality proof; the oracle's checker)
+    certified = certify_state(G, g, host_cap, flow_after)
 
     # ---- the same batches repaired by Dynamic Push-Pull (Alg. 8) ----------
     pp, Gp = None, None
@@ -610,7 +641,7 @@ def main():
     if not args.no_sizes:
         empty = (torch.zeros(0, dtype=torch.int32, device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"))
         for j, k in enumerate((1_000, 10_000, 100_000, 1_000_000)):
-            bs = make_batches(host_cap, k, 3, 20_000 + 10 * j)
+            bs = make_batches(host_cap, k, args.size_batches, 20_000 + 100 * j)
             dyn, sta, ppt = [], [], []
             for b in bs:
                 ids = torch.from_numpy(b.edge_id).cuda()
@@ -629,11 +660,13 @@ def main():
                 sta.append(s0.elapsed_time(s1))
             G.sync()
             d, s = statistics.median(dyn), statistics.median(sta)
-            sizes[str(k)] = {"dynamic_ms": round(d, 4), "static_recompute_ms": round(s, 4),
-                             "speedup": round(s / d, 3), "frac_of_edges": round(k / g.m, 6)}
+            sizes[str(k)] = {"batches": len(bs), "dynamic_ms": round(d, 4), "static_recompute_ms": round(s, 4),
+                             "speedup": round(s / d, 3), "frac_of_edges": round(k / g.m, 6),
+                             "dynamic_spread_ms": spread(dyn), "static_spread_ms": spread(sta)}
             if ppt:
                 pm = statistics.median(ppt)
-                sizes[str(k)].update(push_pull_ms=round(pm, 4), push_pull_speedup=round(s / pm, 3))
+                sizes[str(k)].update(push_pull_ms=round(pm, 4), push_pull_speedup=round(s / pm, 3),
+                                     push_pull_spread_ms=spread(ppt))
     if Gp is not None:
         Gp.close()
 
@@ -641,6 +674,11 @@ def main():
     cpu = None
     if rank == 0 and world >= 1 and args.cpu_sample != 0:
         cpu = cpu_oracle_sample(g, args)
+        # the sample recomputes the values after the first batches of the same
+        # sequence the GPU repaired: compare them one by one
+        want = cpu.pop("flows")
+        cpu["values_equal_oracle"] = all(flows[i] == f for i, f in enumerate(want) if i < len(flows))
+        cpu["values_compared"] = min(len(want), len(flows))
 
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):
@@ -655,11 +693,11 @@ def main():
 
     grid = None
     if not args.no_grid and rank == 0:
-        grid = grid_measurement(5, flush, peak)
+        grid = grid_measurement(args.grid_batches, flush, peak)
 
     serving = None
     if not args.no_serve and rank == 0:
-        serving = serving_measurement((100.0, 1000.0), 4.0)
+        serving = serving_measurement((100.0, 300.0, 600.0, 1000.0), 3.0)
 
     if dist:
         dist.destroy_process_group()
@@ -681,13 +719,20 @@ def main():
                        "min": min(times), "max": max(times)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "traffic_source": ("recorded: an ncu capture of this kernel source "
+                                        "(profiles/k_solve_rmat20_batch100k.md), not measured in this run")
+                     if traffic is not None else None,
                      "peak_source": peak_src, "kernel": "k_solve",
                      "algorithmic_bytes_per_launch": int(mean_bytes), "kernel_source": khash},
         "counters_per_step": {k: v / args.steps for k, v in stats_acc.items()},
+        "policy_choices": None if args.policy == "fixed" else {
+            "recompute": sum(c[0] for c in chosen),
+            "kernel_cycles": sorted({c[1] for c in chosen}),
+            "modes": {name: sum(c[2] == m for c in chosen) for name, m in MODES.items()}},
         "sizes": sizes,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * args.batch,
                 "d2h_bytes_per_step": 16},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if args.policy != "fixed" else 1),   # k_solve (+ k_policy) per step
         "clocks": clk,
         "cpu_baseline": cpu,
         "checks": {"flow_initial": flow0, "flow_final": flow_after, "certified": certified},

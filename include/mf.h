@@ -41,6 +41,10 @@ extern "C" {
 #define MF_ENOTSOLVED  4  /* updates or queries before a successful mf_solve       */
 #define MF_ETIMEOUT    5  /* the device loop reached max_iters or a device wait
                              reached its time limit; state invalid until mf_solve */
+#define MF_ECHECK      6  /* a device-side consistency check of debug_checks
+                             failed (an out-of-range list entry, or an excess,
+                             residual pair or residual mirror that disagrees
+                             with the arcs); state invalid until mf_solve    */
 
 /* ---- flags of mf_apply_updates / mf_min_cut / export / import ------------ */
 #define MF_HOST_PTRS    0x0  /* pointer arguments are host memory (default)      */
@@ -55,17 +59,22 @@ extern "C" {
  * FIXED    always the dynamic repair with the graph's KERNELCYCLES (default)
  * PLAIN    dynamic repair when the batch holds at most 1 % of the edges,
  *          else a static recompute; KERNELCYCLES = average degree (Sec. 6.1)
- * LEARNED  the policy network (mf_mlp_*) chooses repair or recompute and
- *          KERNELCYCLES from 12 batch features; it falls back to PLAIN on
- *          any non-finite or out-of-range input */
+ * LEARNED  the policy network (mf_mlp_*) chooses repair or recompute,
+ *          KERNELCYCLES and the processing mode of the repair (data-driven,
+ *          topology-driven, or -- on a graph created with MF_MODE_PUSH_PULL,
+ *          which keeps the exact cut that Alg. 8 starts from -- Dynamic
+ *          Push-Pull; on other graphs a push-pull choice runs data-driven)
+ *          from 12 batch features; it falls back to PLAIN (and the graph's
+ *          own mode) on any non-finite or out-of-range input */
 #define MF_POLICY_FIXED   0
 #define MF_POLICY_PLAIN   1
 #define MF_POLICY_LEARNED 2
 
 /* ---- processing modes (Sec. 5.2 / 5.3) ---------------------------------- */
 #define MF_MODE_DATA_DRIVEN 0  /* worklist of active vertices (Sec. 5.3)         */
-#define MF_MODE_TOPOLOGY    1  /* the first push/relabel round of each iteration
-                                  visits every vertex id (Sec. 5.2)            */
+#define MF_MODE_TOPOLOGY    1  /* every push/relabel round visits every vertex
+                                  id and serves the active ones, with no
+                                  worklist (Sec. 5.2)                          */
 #define MF_MODE_PUSH_PULL   2  /* repairs by Dynamic Push-Pull (Alg. 8, Sec. 4.2):
                                   saturate the arcs across the previous cut,
                                   push on its sink side and pull on its source
@@ -97,7 +106,16 @@ typedef struct mf_graph mf_graph;
  *                 per loop iteration; passing it reports MF_ETIMEOUT.
  *                 0 = 60000.
  *  alloc / free   device allocator callbacks (both NULL = cudaMalloc/cudaFree).
- *                 alloc(bytes, ctx) returns a device pointer or NULL. */
+ *                 alloc(bytes, ctx) returns a device pointer or NULL.
+ *  debug_checks   non-zero: every solve/repair kernel checks the vertex ids it
+ *                 reads from its lists and queues (out of range: the entry is
+ *                 skipped) and, at its end, re-derives the state's invariants
+ *                 over all arcs -- e(v) = sum over v's arcs of (r - cap) (the
+ *                 incremental excess of the repair equals the full recount of
+ *                 Alg. 4 line 2), r >= 0, r(a) + r(rev a) = cap(a) + cap(rev a),
+ *                 and the residual mirror; a failure sets a status bit that
+ *                 mf_flow_value reports as MF_ECHECK.  Never traps.  Costs one
+ *                 O(arcs) pass per kernel.  0 = off. */
 typedef struct mf_options {
     int32_t kernel_cycles;
     int32_t mode;
@@ -107,6 +125,7 @@ typedef struct mf_options {
     void *(*alloc)(size_t bytes, void *ctx);
     void (*free)(void *ptr, void *ctx);
     void *alloc_ctx;
+    int32_t debug_checks;
 } mf_options;
 
 /* Counters of the last mf_solve / mf_apply_updates (device-side counts).
@@ -176,6 +195,10 @@ typedef struct mf_stats {
     int32_t kernel_cycles;
     int32_t grid_blocks;
     int32_t block_threads;
+    int32_t policy_mode;      /* processing mode the policy chose for the last
+                                 batch (MF_MODE_*; the graph's own without a
+                                 learned policy)                             */
+    int32_t reserved0;
 } mf_stats;
 
 /* Fill *opt with the defaults described above. */
@@ -253,6 +276,12 @@ int mf_device_bytes(const mf_graph *g, int64_t *bytes);
 /* CTAs of the graph's persistent kernel (options.grid_blocks after clamping). */
 int mf_grid_blocks(const mf_graph *g, int32_t *blocks);
 
+/* CTAs of the graph's following solve/repair launches (clamped to one full
+ * wave; a launch captured in a CUDA graph keeps the size it was captured
+ * with).  Any size gives the same results; fewer CTAs leave SMs to other
+ * graphs' repairs.  Does not synchronise.  MF_EINVAL if blocks < 1. */
+int mf_set_grid_blocks(mf_graph *g, int32_t blocks);
+
 /* Wait for the graph's work and report the status of the last solve/repair:
  * MF_OK, MF_EINVAL (rejected batch, reported once), MF_ETIMEOUT. */
 int mf_sync(mf_graph *g);
@@ -291,6 +320,11 @@ int mf_export_state(mf_graph *g, int32_t *r, int64_t *excess, int32_t *height, i
 int mf_import_state(mf_graph *g, const int32_t *r, const int64_t *excess, const int32_t *height,
                     int32_t flags);
 
+/* Change the wall-clock limit of the graph's following solve/repair kernels
+ * (time_limit_ms of mf_options; 0 = 60000).  Takes effect at the next launch;
+ * does not synchronise.  Returns MF_EINVAL for a negative value. */
+int mf_set_time_limit(mf_graph *g, int32_t time_limit_ms);
+
 /* Free all device memory of the graph (synchronises first).  NULL is a no-op. */
 void mf_destroy(mf_graph *g);
 
@@ -305,9 +339,20 @@ void mf_destroy(mf_graph *g);
  *   n, arcs        vertices (2 .. 131072) and Bi-CSR arcs (0 .. 2097152);
  *                  larger graphs are rejected with MF_EINVAL
  *   row [n+1], head/rev/cap [arcs]   the Bi-CSR of mf_bicsr_host, int32,
- *                  device memory, read only
+ *                  device memory, read only, head and r 16-byte aligned for
+ *                  the fastest path (any alignment works).  mf_bicsr_host
+ *                  returns the offsets arc_row as int64: the caller narrows
+ *                  them to int32 for row (they fit, arcs <= 2097152).  The
+ *                  arrays must be mf_bicsr_host's output unchanged (row[n] ==
+ *                  arcs, heads in range, rev an involution pairing u -> v with
+ *                  v -> u): they are not validated, and inconsistent arrays
+ *                  make the kernel read out of bounds.
  *   s, t           source and sink
- *   kernel_cycles  as mf_options (0 = default)
+ *   kernel_cycles  as mf_options; 0 = the average Bi-CSR degree
+ *                  max(1, round((arcs / 2) / n)), computed from arcs because
+ *                  the input edge count is not passed: where the Bi-CSR merged
+ *                  antiparallel edges it can differ from mf_create's default
+ *                  (same values, other timings) -- pass it explicitly to match
  *   r [arcs] int32, excess [n] int64, height [n] int32: device outputs --
  *                  the final residuals, excesses and heights (the min cut is
  *                  {v : height[v] >= n})
@@ -344,30 +389,33 @@ int mf_policy_features(mf_graph *g, int64_t k, const int32_t *edge_id, const int
                        int32_t flags, float *features);
 
 /* ---- the policy network (device arrays, float32, stream-ordered) -------
- * Sizes: inputs 12, outputs 2, trained parameters, all parameters (with the
+ * Sizes: inputs 12, outputs 5 (repair-vs-recompute logit, log2
+ * KERNELCYCLES, and the logits of the processing modes data-driven,
+ * topology-driven, push-pull), trained parameters, all parameters (with the
  * input normalisation mu[12], sd[12] at the end). */
 int mf_mlp_sizes(int32_t *n_in, int32_t *n_out, int32_t *n_trained, int32_t *n_total);
 
 /* Bytes of the caller-provided workspace for mini-batches of `batch`. */
 int64_t mf_mlp_workspace_bytes(int32_t batch);
 
-/* Y[n x 2] = network(X[n x 12]); P: n_total parameters. */
+/* Y[n x 5] = network(X[n x 12]); P: n_total parameters. */
 int mf_mlp_forward(const float *P, const float *X, int32_t n, float *Y, void *stream);
 
 /* Gradient (grad [n_trained]) and value (loss [1]) over all n samples of the
- * mean loss BCE(y0, t0) + wkc * (y1 - t1)^2 / 2.  workspace:
+ * mean loss BCE(y0, t0) + wkc * (y1 - t1)^2 / 2 + wmode * CE(softmax(y2..y4),
+ * t2), t2 the index 0/1/2 of the target mode stored as a float.  workspace:
  * mf_mlp_workspace_bytes(n). */
-int mf_mlp_grad(const float *P, const float *X, const float *T0, const float *T1, int32_t n, float wkc,
-                float *grad, float *loss, void *workspace, void *stream);
+int mf_mlp_grad(const float *P, const float *X, const float *T0, const float *T1, const float *T2, int32_t n,
+                float wkc, float wmode, float *grad, float *loss, void *workspace, void *stream);
 
 /* `steps` Adam steps (lr; betas 0.9, 0.999) on mini-batches of `batch`
- * consecutive samples taken cyclically from X/T0/T1 (shuffle beforehand).
+ * consecutive samples taken cyclically from X/T0/T1/T2 (shuffle beforehand).
  * M, V: Adam moments [n_trained] (zero before the first step); step0: steps
  * taken before (for the bias correction).  loss_hist [steps] or NULL receives
  * each mini-batch loss.  workspace: mf_mlp_workspace_bytes(batch). */
-int mf_mlp_train(float *P, float *M, float *V, const float *X, const float *T0, const float *T1, int32_t n,
-                 int32_t steps, int32_t batch, float lr, float wkc, int32_t step0, float *loss_hist,
-                 void *workspace, void *stream);
+int mf_mlp_train(float *P, float *M, float *V, const float *X, const float *T0, const float *T1, const float *T2,
+                 int32_t n, int32_t steps, int32_t batch, float lr, float wkc, float wmode, int32_t step0,
+                 float *loss_hist, void *workspace, void *stream);
 
 /* ---- serving several resident graphs (continuous batching) --------------
  * A server owns a scheduler thread.  Graphs (created, policy set and solved
@@ -377,10 +425,15 @@ int mf_mlp_train(float *P, float *M, float *V, const float *X, const float *T0, 
  * all repairs in flight stay within sm_slots (so that their persistent grids
  * are co-resident and overlap), and their device staging fits the HBM budget
  * left after the resident graphs; requests that do not fit wait while later
- * ones for other graphs may start.  Each graph's repair is captured once in
- * a CUDA graph and replayed (use_cuda_graphs; if capture fails the server
- * launches directly and reports fewer captured graphs).  A graph belongs to
- * the server once added: call nothing else on it until mf_server_destroy. */
+ * ones for other graphs may start.  A request's repair runs on a grid sized
+ * to its batch: the graph's full grid for batches above 20,000 entries and
+ * for recomputes, half of it above 2,000 entries, a quarter below (at least
+ * one CTA), so that small repairs are admitted beside large ones.  Each
+ * graph's repair and recompute are captured once per grid size in CUDA
+ * graphs and replayed (use_cuda_graphs; if a capture fails the server
+ * launches that case directly and reports fewer captured graphs; up to six
+ * per graph).  A graph belongs to the server once added: call nothing else
+ * on it until mf_server_destroy, and destroy the server before its graphs. */
 typedef struct mf_server mf_server;
 typedef struct mf_server_options {
     int64_t hbm_budget_bytes;   /* 0 = the device's total memory                  */
@@ -390,10 +443,12 @@ typedef struct mf_server_options {
 typedef struct mf_server_stats {
     int64_t submitted, completed, failed;
     int32_t max_inflight;       /* most repairs in flight at once                 */
-    int32_t graphs, captured_graphs;
+    int32_t graphs, captured_graphs;  /* captured: CUDA graphs instantiated      */
     int32_t reserved;
     double p50_us, p99_us, mean_us;  /* submit-to-completion latency             */
     double makespan_s;          /* first submit to last completion                */
+    int64_t replays;            /* requests served by replaying a captured graph  */
+    int64_t direct_launches;    /* requests launched without a captured graph     */
 } mf_server_stats;
 
 int mf_server_options_default(mf_server_options *opt);
@@ -410,7 +465,9 @@ int mf_server_submit(mf_server *s, int32_t graph, int64_t k, const int32_t *edge
  * MF_ETIMEOUT, MF_ECUDA) and *latency_us (submit to completion) are set. */
 int mf_server_poll(mf_server *s, int64_t ticket, int32_t *done, int64_t *flow, int32_t *code,
                    double *latency_us);
-/* Wait until every submitted request completed. */
+/* Wait until every submitted request completed.  Returns MF_OK once they
+ * have, whether or not they succeeded: each request's code comes from
+ * mf_server_poll, and mf_server_stats counts the failed ones. */
 int mf_server_drain(mf_server *s);
 int mf_server_stats_get(mf_server *s, mf_server_stats *out);
 /* Forget the latencies and counts of completed requests. */

@@ -13,13 +13,13 @@ import numpy as np
 
 from . import _build
 
-MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_ENOTSOLVED, MF_ETIMEOUT = range(6)
+MF_OK, MF_EINVAL, MF_ENOMEM, MF_ECUDA, MF_ENOTSOLVED, MF_ETIMEOUT, MF_ECHECK = range(7)
 MF_HOST_PTRS, MF_DEVICE_PTRS, MF_DELTA, MF_RECOMPUTE = 0x0, 0x1, 0x2, 0x4
 MF_POLICY_FIXED, MF_POLICY_PLAIN, MF_POLICY_LEARNED = 0, 1, 2
 MF_MODE_DATA_DRIVEN, MF_MODE_TOPOLOGY, MF_MODE_PUSH_PULL = 0, 1, 2
 
 ERROR_NAMES = {MF_EINVAL: "MF_EINVAL", MF_ENOMEM: "MF_ENOMEM", MF_ECUDA: "MF_ECUDA",
-               MF_ENOTSOLVED: "MF_ENOTSOLVED", MF_ETIMEOUT: "MF_ETIMEOUT"}
+               MF_ENOTSOLVED: "MF_ENOTSOLVED", MF_ETIMEOUT: "MF_ETIMEOUT", MF_ECHECK: "MF_ECHECK"}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -29,7 +29,7 @@ class Options(ctypes.Structure):
     _fields_ = [("kernel_cycles", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("max_iters", ctypes.c_int64), ("grid_blocks", ctypes.c_int32),
                 ("time_limit_ms", ctypes.c_int32), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_ctx", ctypes.c_void_p)]
+                ("alloc_ctx", ctypes.c_void_p), ("debug_checks", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -40,10 +40,10 @@ class Stats(ctypes.Structure):
         "hub_cycles", "barriers", "bfs_bottom_up_levels", "pr_rounds")] + [
         (f, ctypes.c_int32) for f in ("policy_kind", "policy_kernel_cycles", "policy_fallback",
                                       "exit_kind")] + [(f, ctypes.c_int32) for f in ("status", "kernel_cycles", "grid_blocks",
-                                                   "block_threads")]
+                                                   "block_threads", "policy_mode", "reserved0")]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved0"}
 
 
 # every symbol include/mf.h declares (checked by the CPU test suite)
@@ -51,9 +51,9 @@ EXPORTED = ["mf_options_default", "mf_create", "mf_cap_limit", "mf_solve", "mf_a
             "mf_sync", "mf_flow_value", "mf_min_cut", "mf_stats_get", "mf_sizes",
             "mf_export_graph", "mf_export_state", "mf_import_state", "mf_destroy",
             "mf_strerror", "mf_version", "mf_last_error", "mf_bicsr_host", "mf_solve_bicsr_noalloc",
-            "mf_trace_enable", "mf_trace_read", "mf_set_policy", "mf_policy_features",
+            "mf_trace_enable", "mf_trace_read", "mf_set_time_limit", "mf_set_policy", "mf_policy_features",
             "mf_mlp_sizes", "mf_mlp_workspace_bytes", "mf_mlp_forward", "mf_mlp_grad", "mf_mlp_train",
-            "mf_apply_updates_dev", "mf_flow_value_async", "mf_set_stream", "mf_device_bytes", "mf_grid_blocks",
+            "mf_apply_updates_dev", "mf_flow_value_async", "mf_set_stream", "mf_device_bytes", "mf_grid_blocks", "mf_set_grid_blocks",
             "mf_server_options_default", "mf_server_create", "mf_server_add_graph", "mf_server_submit",
             "mf_server_poll", "mf_server_drain", "mf_server_stats_get", "mf_server_reset_stats",
             "mf_server_destroy"]
@@ -110,20 +110,22 @@ def lib(build_if_missing: bool = False):
         "mf_bicsr_host": ([i32, i64, P, P, P, i32, i32, P, P, P, P, P, P, P], ctypes.c_int),
         "mf_solve_bicsr_noalloc": ([i32, i64, P, P, P, P, i32, i32, i32, P, P, P, P, P], ctypes.c_int),
         "mf_trace_enable": ([P, i32], ctypes.c_int),
+        "mf_set_time_limit": ([P, i32], ctypes.c_int),
         "mf_trace_read": ([P, P, i32, P], ctypes.c_int),
         "mf_set_policy": ([P, i32, P], ctypes.c_int),
         "mf_policy_features": ([P, i64, P, P, i32, P], ctypes.c_int),
         "mf_mlp_sizes": ([P, P, P, P], ctypes.c_int),
         "mf_mlp_workspace_bytes": ([i32], i64),
         "mf_mlp_forward": ([P, P, i32, P, P], ctypes.c_int),
-        "mf_mlp_grad": ([P, P, P, P, i32, ctypes.c_float, P, P, P, P], ctypes.c_int),
-        "mf_mlp_train": ([P, P, P, P, P, P, i32, i32, i32, ctypes.c_float, ctypes.c_float, i32, P, P, P],
-                         ctypes.c_int),
+        "mf_mlp_grad": ([P, P, P, P, P, i32, ctypes.c_float, ctypes.c_float, P, P, P, P], ctypes.c_int),
+        "mf_mlp_train": ([P, P, P, P, P, P, P, i32, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32,
+                          P, P, P], ctypes.c_int),
         "mf_apply_updates_dev": ([P, P, i64, P, P, i32, P], ctypes.c_int),
         "mf_flow_value_async": ([P, P, P], ctypes.c_int),
         "mf_set_stream": ([P, P], ctypes.c_int),
         "mf_device_bytes": ([P, P], ctypes.c_int),
         "mf_grid_blocks": ([P, P], ctypes.c_int),
+        "mf_set_grid_blocks": ([P, i32], ctypes.c_int),
         "mf_server_options_default": ([P], ctypes.c_int),
         "mf_server_create": ([P, P], ctypes.c_int),
         "mf_server_add_graph": ([P, P, i64, P], ctypes.c_int),
@@ -216,7 +218,7 @@ class MaxFlowGraph:
 
     def __init__(self, n, row_ptr, col, cap, s, t, *, kernel_cycles=0, max_iters=0,
                  grid_blocks=0, time_limit_ms=0, mode=MF_MODE_DATA_DRIVEN, torch_allocator=False,
-                 stream=None):
+                 debug_checks=False, stream=None):
         L = lib()
         self._opt = Options()
         L.mf_options_default(ctypes.byref(self._opt))
@@ -225,6 +227,7 @@ class MaxFlowGraph:
         self._opt.grid_blocks = grid_blocks
         self._opt.time_limit_ms = time_limit_ms
         self._opt.mode = mode
+        self._opt.debug_checks = 1 if debug_checks else 0
         self._keep = []
         if torch_allocator:
             torch = _torch()
@@ -288,6 +291,10 @@ class MaxFlowGraph:
 
     def sync(self):
         _check(lib().mf_sync(self._h), "mf_sync")
+
+    def set_time_limit(self, time_limit_ms):
+        """Wall-clock limit of the following solve/repair kernels (0 = 60 s)."""
+        _check(lib().mf_set_time_limit(self._h, int(time_limit_ms)), "mf_set_time_limit")
 
     def flow_value(self) -> int:
         out = ctypes.c_int64(0)
@@ -378,7 +385,7 @@ class ServerStats(ctypes.Structure):
                 ("max_inflight", ctypes.c_int32), ("graphs", ctypes.c_int32),
                 ("captured_graphs", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
-                ("makespan_s", ctypes.c_double)]
+                ("makespan_s", ctypes.c_double), ("replays", ctypes.c_int64), ("direct_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

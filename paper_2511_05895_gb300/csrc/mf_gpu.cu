@@ -61,7 +61,8 @@ constexpr int ST_EINVAL = 1;   // rejected batch (state unchanged)
 constexpr int ST_ITERS = 2;    // max_iters reached
 constexpr int ST_WAIT = 4;     // a grid-barrier wait reached its time limit
 constexpr int ST_TIME = 8;     // the kernel ran past its wall-clock limit
-constexpr int ST_STICKY = ST_ITERS | ST_WAIT | ST_TIME;
+constexpr int ST_CHECK = 16;   // a debug_checks consistency check failed
+constexpr int ST_STICKY = ST_ITERS | ST_WAIT | ST_TIME | ST_CHECK;
 
 // JOB_REFRESH recomputes exact BFS heights (and the exact cut S = {h >= n})
 // for a state whose last solve stopped without a final BFS; it does nothing
@@ -118,6 +119,7 @@ struct Ctl {
     unsigned long long t_start;  // globaltimer at kernel entry
     int pol_kind;         // policy decision for the next JOB_AUTO launch
     int pol_kc;
+    int pol_mode;         // processing mode chosen for it (MF_MODE_*)
     int pol_fallback;     // 1 if the learned policy fell back to the plain rule
     float feat[12];       // features of the last batch the policy kernel saw
     long long pol_acc[3]; // (z) k_policy's batch sums: increments, entries at s or t, sum |delta|
@@ -146,6 +148,7 @@ struct Ctl {
     alignas(128) int aq_over;   // (z) an active vertex was left out (generation cap, full queue)
     int aq_maxgen;              // (z) highest generation enqueued
     alignas(128) int aq_fin;    // (z) every queued entry has been processed
+    long long chk_where;        // first failed debug check: kind << 40 | index (kept until mf_solve)
 };
 
 enum Stat {
@@ -202,6 +205,7 @@ constexpr unsigned char kPartT = 0, kPartS = 1, kPartP = 2;
 
 struct Job {
     int kind, k, flags, kc, mode;
+    int debug;           // debug_checks: list-entry bounds and the end-of-kernel invariants
     int exact_exit;      // 1: stop only after a BFS finds no active vertex
     int pp;              // 1: a repair by Dynamic Push-Pull (Alg. 8) when the cut is exact
     int sink_sat;        // 1: a solve from zero flow also saturates the arcs into t
@@ -1361,8 +1365,8 @@ __device__ __forceinline__ long long hub_move_item(const DevGraph &G, int a0, in
         // item measured faster: its pushes spread over the hub's arcs)
         if (skip_done && bcast_ld(rem) <= 0) break;
         ArcRound R;
+        // (the arcs H1 scanned in this cycle: not counted again)
         load_round_t<PULL, true>(G, a0, a1, R, pt, side);
-        K.pr_arcs += round_arcs(a0, a1);
         int ra[kIlp];
         long long incl[kIlp], tot = 0;
 #pragma unroll
@@ -1401,6 +1405,22 @@ __device__ __forceinline__ void flush_counters(Counters &K, long long *st) {
         if ((threadIdx.x & 31) == 0 && v) add_ll(&st[idx[i]], v);
     }
     K = Counters{};
+}
+
+// debug_checks: record a failed check (the first one's kind and index) and
+// make the state invalid until the next mf_solve; the caller skips the
+// access.  Kinds: 1 list entry out of range, 2 excess != net inflow, 3
+// residual pair or mirror inconsistent.
+__device__ __forceinline__ void check_fail(Ctl *C, int kind, long long where) {
+    if ((atomicOr(&C->status, ST_CHECK) & ST_CHECK) == 0)
+        C->chk_where = ((long long)kind << 40) | (where & 0xffffffffffll);
+}
+
+// A vertex id read from a list or queue, checked when debug_checks is on.
+__device__ __forceinline__ bool vertex_ok(const Job &J, Ctl *C, int u, int n) {
+    if (!J.debug || (u >= 0 && u < n)) return true;
+    check_fail(C, 1, u);
+    return false;
 }
 
 // ------------------------------------------------------------ the kernel --
@@ -1476,10 +1496,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     const unsigned stamp_base = __ldcg(&C->stamp_base) + 1u;
     // JOB_AUTO: the policy kernel launched just before chose repair or
     // recompute and KERNELCYCLES
-    int kind = J.kind, kc = J.kc;
+    int kind = J.kind, kc = J.kc, jmode = J.mode;
+    bool pp_pick = true;   // a fixed job of a push-pull graph repairs by push-pull
     if (kind == JOB_AUTO) {
         kind = lcg(&C->pol_kind);
         kc = lcg(&C->pol_kc);
+        jmode = lcg(&C->pol_mode);
+        pp_pick = jmode == MF_MODE_PUSH_PULL;
+        if (pp_pick) jmode = MF_MODE_DATA_DRIVEN;   // the plain loop of push-pull's stage 2
     }
     if (kind == JOB_REFRESH && lcg(&C->heights_exact)) return;
     const bool batch_job = kind == JOB_REPAIR || kind == JOB_RECOMPUTE;
@@ -1494,7 +1518,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
 
     // Dynamic Push-Pull (Alg. 8) needs the exact cut of the previous state:
     // T = {h < n} can reach a sink, S = {h >= n} cannot
-    const bool pp = PP && J.pp && kind == JOB_REPAIR && G.part && lcg(&C->cut_exact);
+    const bool pp = PP && J.pp && pp_pick && kind == JOB_REPAIR && G.part && lcg(&C->cut_exact);
     if (pp)
         for (long long v = gtid; v < n; v += gthreads) G.part[v] = lcg(&G.h[v]) < n ? kPartT : kPartS;
 
@@ -1876,8 +1900,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     const int idx = grp * gs + lane;
                     int beg = 0, deg = 0;
                     bool fwd = false;
-                    if (lane < gs && idx < cur) {
-                        const int u = lcg(&F[idx]);
+                    const int u = (lane < gs && idx < cur) ? lcg(&F[idx]) : 0;
+                    if (lane < gs && idx < cur && vertex_ok(J, C, u, n)) {
                         fwd = dual && G.part[u] == kPartS;
                         beg = __ldg(&G.row[u]);
                         deg = __ldg(&G.row[u + 1]) - beg;
@@ -1990,14 +2014,15 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             }
             // the data-driven and push-pull modes run PushRelabel from the
             // activation queue; the topology-driven mode in rounds
-            const bool qmode = J.mode != MF_MODE_TOPOLOGY && G.aq != nullptr;
+            const bool qmode = jmode != MF_MODE_TOPOLOGY && G.aq != nullptr;
             const ActList AL0{&C->wcnt, G.wl,   wstamp,     rstamp_it, pcnt, (pass & 1) ? G.hl : G.hl2,
                               hstamp,   qmode ? G.aq : nullptr, G.qc, 0, max_rounds, C};
             bool pass_hubs_clean = true;
             if (nhp > 0) {
                 pass_hubs_clean = false;
                 for (int i = gwarp; i < nhp; i += nwarps) {
-                    const int u = lcg(&HL[i]);
+                    const int u = bcast_ld(&HL[i]);
+                    if (!vertex_ok(J, C, u, n)) continue;   // warp-uniform
                     const int beg = __ldg(&G.row[u]);
                     const int nc = (__ldg(&G.row[u + 1]) - beg + kPrChunk - 1) / kPrChunk;
                     int pos = 0;
@@ -2210,7 +2235,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 for (int i = gwarp;; i += nwarps) {
                     int u = -1, gen = 0;
                     if (i < n0) {
-                        u = lcg(&G.wl[i]);
+                        u = bcast_ld(&G.wl[i]);
                     } else {
                         int q = 0;
                         unsigned long long slot = 0;
@@ -2242,7 +2267,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     }
                     const ActList AL{nullptr, nullptr, wstamp, rstamp_it, pcnt, AL0.hlist, hstamp,
                                      G.aq,    G.qc,    gen + 1, max_rounds, C};
-                    if (stage == 1) {
+                    if (!vertex_ok(J, C, u, n)) {
+                        // skipped; still counted as processed below
+                    } else if (stage == 1) {
                         const unsigned char side = G.part[u];
                         if (side == kPartS)
                             push_relabel_warp_t<true>(G, u, kc, AL, G.part, side, stg, K);
@@ -2266,7 +2293,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 }
                 // (the counters are zeroed for the next pass after its set-up
                 // barrier, when every thread has read them)
-            } else if (!qmode && (cnt > 0 || (pass == 0 && J.mode == MF_MODE_TOPOLOGY))) {
+            } else if (!qmode && (cnt > 0 || (pass == 0 && jmode == MF_MODE_TOPOLOGY))) {
                 pass_rounds_clean = false;
                 const int *list = G.wl;
                 for (int rd = 0;; ++rd) {
@@ -2277,9 +2304,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                         ST[S_ROUNDS] += 1;
                         ST[S_WL] += cnt;
                     }
-                    if (rd == 0 && pass == 0 && J.mode == MF_MODE_TOPOLOGY) {
-                        // topology-driven (Sec. 5.2): every vertex id is visited;
-                        // each warp takes 32 ids and serves the active ones
+                    if (jmode == MF_MODE_TOPOLOGY) {
+                        // topology-driven (Sec. 5.2): every round visits every
+                        // vertex id and serves the active ones, each warp 32 ids
+                        // at a time (no worklist: the round lists only tell
+                        // whether another round has work)
                         for (int grp = gwarp; grp * 32 < n; grp += nwarps) {
                             const int base = grp * 32;
                             const int v = base + lane;
@@ -2331,7 +2360,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         const unsigned char *ptc = stage ? G.part : nullptr;
         const int nrl = lcg(&C->rlcnt);
         for (int i = gwarp; i < nrl; i += nwarps) {
-            const int u = lcg(&G.rl[i]);
+            const int u = bcast_ld(&G.rl[i]);
+            if (!vertex_ok(J, C, u, n)) continue;   // warp-uniform
             const unsigned char side = ptc ? ptc[u] : kPartT;
             if (side == kPartS)
                 remove_invalid_warp_t<true>(G, u, &C->ri_moved[par], ptc, side, K);
@@ -2341,7 +2371,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         const int nri = lcg(&C->rhcnt);
         for (int w = gwarp; w < nri; w += nwarps) {
             const int2 item = lcg(&G.hri[w]);
-            const int u = item.x;
+            const int u = __shfl_sync(kFull, item.x, 0);
+            if (!vertex_ok(J, C, u, n)) continue;   // warp-uniform
             const int hu = bcast_ld(&G.h[u]);
             const int a1 = min(item.y + kPrChunk, __ldg(&G.row[u + 1]));
             const unsigned char side = stage == 1 ? G.part[u] : (stage == 2 ? kPartP : kPartT);
@@ -2406,6 +2437,31 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         MF_SYNC_T(S_T_RESET, 3, 0, 0);
     }
 
+    // ---- debug_checks: the state's invariants over all arcs ----------------
+    // e(v) = sum over v's arcs of (r - cap) (the incremental excess updates
+    // of the repair equal the full recount of Alg. 4 line 2), r >= 0, the
+    // residuals of an arc pair add up to the pair's capacities, and the
+    // mirror rr(a) = r(rev a).  One warp per vertex.
+    if (J.debug) {
+        for (int v = gwarp; v < n; v += nwarps) {
+            const int a0 = __ldg(&G.row[v]), a1 = __ldg(&G.row[v + 1]);
+            long long in = 0;
+            bool bad = false;
+            for (int a = a0 + lane; a < a1; a += 32) {
+                const int b = __ldg(&G.rev[a]);
+                const int ra = lcg(&G.r[a]), rb = lcg(&G.r[b]);
+                in += (long long)ra - lcg(&G.cap[a]);
+                if (ra < 0 || (long long)ra + rb != (long long)lcg(&G.cap[a]) + lcg(&G.cap[b]) ||
+                    lcg(&G.rr[a]) != rb) {
+                    if (!bad) check_fail(C, 3, a);
+                    bad = true;
+                }
+            }
+            in = warp_sum(in);
+            if (lane == 0 && in != lcg(&G.e[v])) check_fail(C, 2, v);
+        }
+    }
+
     // ---- result and statistics -------------------------------------------
     if (gtid == 0) {
         // dacc: deficits at the last height init, or recounted at a clean
@@ -2442,8 +2498,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
 #undef TR
 
 // ------------------------------------------------------------- policy --
+static_assert(MF_MODE_DATA_DRIVEN == 0 && MF_MODE_TOPOLOGY == 1 && MF_MODE_PUSH_PULL == 2,
+              "the network's mode outputs 2, 3, 4 are the modes in this order");
+
 struct PolicyJob {
     int k, flags, mode, kc_plain, max_deg;
+    int gmode;             // the graph's own processing mode (MF_MODE_*)
+    int pp_ok;             // the graph can repair by Dynamic Push-Pull
     const int *k_dev;      // if set, the batch size is read from device memory
     const int *ids, *caps;
     const float *params;   // network parameters (mf_mlp.cuh), or null
@@ -2554,9 +2615,10 @@ __global__ void __launch_bounds__(256) k_policy(DevGraph G, PolicyJob PJ) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        int kind, kc;
+        int kind, kc, mode = PJ.gmode;
         bool fallback = fb != 0;
-        if (!fallback && !(isfinite(y[0]) && isfinite(y[1]))) fallback = true;
+        for (int o = 0; o < mlp::kOut && !fallback; ++o)
+            if (!isfinite(y[o])) fallback = true;
         if (fallback) {
             kind = (long long)PJ.k * 100 <= (long long)G.m ? JOB_REPAIR : JOB_RECOMPUTE;
             kc = PJ.kc_plain;
@@ -2564,9 +2626,18 @@ __global__ void __launch_bounds__(256) k_policy(DevGraph G, PolicyJob PJ) {
             kind = y[0] > 0.f ? JOB_REPAIR : JOB_RECOMPUTE;
             const float l = fminf(fmaxf(rintf(y[1]), 0.f), 6.f);
             kc = 1 << (int)l;
+            // the mode of the largest logit (outputs 2, 3, 4: data-driven,
+            // topology-driven, push-pull); push-pull only where the graph
+            // keeps the exact cut it needs, else the better of the other two
+            int best = 0;
+            for (int c = 1; c < mlp::kModes; ++c)
+                if (y[2 + c] > y[2 + best]) best = c;
+            if (best == MF_MODE_PUSH_PULL && !PJ.pp_ok) best = y[3] > y[2] ? MF_MODE_TOPOLOGY : MF_MODE_DATA_DRIVEN;
+            mode = best;
         }
         C->pol_kind = kind;
         C->pol_kc = kc;
+        C->pol_mode = mode;
         C->pol_fallback = (PJ.mode == MF_POLICY_LEARNED && fallback) ? 1 : 0;
     }
 }
@@ -2632,6 +2703,7 @@ struct mf_graph {
     long long max_iters = 0;
     unsigned long long time_limit_ns = 0;
     int grid = 0, sms = 0;
+    int max_grid = 0;   // one full wave of co-resident CTAs
     mf_options opt{};
     DevGraph dg{};
     std::vector<void *> owned;
@@ -2758,6 +2830,7 @@ int launch(mf_graph *g, const Job &job, cudaStream_t st) {
     DevGraph dg = g->dg;
     Job jb = job;
     jb.st = job.kind == JOB_REFRESH ? g->dg.ctl->st_aux : g->dg.ctl->st;
+    jb.debug = g->opt.debug_checks != 0;
     jb.trace = job.kind == JOB_REFRESH ? nullptr : g->dg.trace;
     void *args[] = {&dg, &jb};
     // a push-pull graph keeps its cut exact (every job ends on a BFS) and
@@ -2786,6 +2859,9 @@ int launch_policy(mf_graph *g, int64_t k, const int *ids, const int *caps, int f
     pj.ids = ids;
     pj.caps = caps;
     pj.params = g->params;
+    pj.gmode = g->opt.mode;
+    pj.pp_ok = g->opt.mode == MF_MODE_PUSH_PULL;
+    cudaGetLastError();   // an earlier, unrelated failure of this thread is not this launch's
     k_policy<<<g->grid, 256, 0, st>>>(g->dg, pj);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(MF_ECUDA, std::string("policy launch: ") + cudaGetErrorString(e));
@@ -2829,6 +2905,14 @@ int refresh_heights(mf_graph *g) {
 }
 
 int status_to_code(mf_graph *g, const Ctl &c) {
+    if (c.status & ST_CHECK) {
+        g->solved = false;
+        static const char *kinds[] = {"?", "list entry out of range", "excess differs from the net inflow",
+                                      "residual pair or mirror inconsistent"};
+        const long long kind = c.chk_where >> 40, where = c.chk_where & 0xffffffffffll;
+        return set_err(MF_ECHECK, std::string("debug check failed: ") + kinds[kind >= 1 && kind <= 3 ? kind : 0] +
+                                      " (index " + std::to_string(where) + ")");
+    }
     if (c.status & ST_STICKY) {
         g->solved = false;
         return set_err(MF_ETIMEOUT, (c.status & ST_WAIT)   ? "device wait reached its time limit"
@@ -2858,6 +2942,7 @@ const char *mf_strerror(int code) {
         case MF_ECUDA: return "CUDA error";
         case MF_ENOTSOLVED: return "graph not solved";
         case MF_ETIMEOUT: return "device loop timeout";
+        case MF_ECHECK: return "device consistency check failed";
         default: return "unknown error";
     }
 }
@@ -2935,6 +3020,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     if (per_sm < 1)
         return fail(MF_ECUDA, "occupancy query failed");
     g->grid = per_sm * g->sms;
+    g->max_grid = g->grid;
     if (g->opt.grid_blocks > 0) g->grid = std::min(g->grid, int(g->opt.grid_blocks));
 
     g->n = n; g->m = m; g->A = H.arcs; g->s = s; g->t = t;
@@ -3109,6 +3195,9 @@ int mf_apply_updates_dev(mf_graph *g, const int32_t *k_dev, int64_t k_max, const
         pj.ids = edge_id;
         pj.caps = new_cap;
         pj.params = g->params;
+        pj.gmode = g->opt.mode;
+        pj.pp_ok = g->opt.mode == MF_MODE_PUSH_PULL;
+        cudaGetLastError();   // an earlier, unrelated failure of this thread is not this launch's
         k_policy<<<g->grid, 256, 0, st>>>(g->dg, pj);
         MF_CUDA(cudaGetLastError());
         j.kind = JOB_AUTO;
@@ -3158,6 +3247,12 @@ int mf_grid_blocks(const mf_graph *g, int32_t *blocks) {
     return MF_OK;
 }
 
+int mf_set_grid_blocks(mf_graph *g, int32_t blocks) {
+    if (!g || blocks < 1) return set_err(MF_EINVAL, "null graph or fewer than one CTA");
+    g->grid = std::min(int(blocks), g->max_grid);
+    return MF_OK;
+}
+
 int mf_sync(mf_graph *g) {
     if (!g) return MF_EINVAL;
     Ctl c;
@@ -3171,8 +3266,12 @@ int mf_flow_value(mf_graph *g, int64_t *out) {
     Ctl c;
     int rc = read_ctl(g, &c, 16);   // status, batch_err, flow
     if (rc) return rc;
+    if (c.status & ST_CHECK) {      // where the check failed, for the message
+        rc = read_ctl(g, &c);
+        if (rc) return rc;
+    }
     rc = status_to_code(g, c);
-    if (rc == MF_ETIMEOUT) return rc;
+    if (rc == MF_ETIMEOUT || rc == MF_ECHECK) return rc;
     if (!g->solved) return set_err(MF_ENOTSOLVED, "call mf_solve first");
     *out = c.flow;
     return rc;
@@ -3186,6 +3285,7 @@ int mf_min_cut(mf_graph *g, uint8_t *side, int32_t flags) {
     if (rc) return rc;
     unsigned char *dst = (flags & MF_DEVICE_PTRS) ? side : g->side_buf;
     int blocks = std::max(1, std::min(g->sms * 4, (g->n + 255) / 256));
+    cudaGetLastError();   // an earlier, unrelated failure of this thread is not this launch's
     k_cut_side<<<blocks, 256, 0, g->last>>>(g->dg.h, g->n, dst);
     MF_CUDA(cudaGetLastError());
     if (!(flags & MF_DEVICE_PTRS))
@@ -3229,6 +3329,7 @@ int mf_stats_get(mf_graph *g, mf_stats *out) {
     out->policy_kind = c.pol_kind == JOB_RECOMPUTE ? 1 : 0;
     out->policy_kernel_cycles = c.pol_kc;
     out->policy_fallback = c.pol_fallback;
+    out->policy_mode = g->policy == MF_POLICY_LEARNED ? c.pol_mode : g->opt.mode;
     out->exit_kind = c.exit_kind;
     out->status = c.status;
     out->kernel_cycles = g->kc;
@@ -3293,9 +3394,17 @@ int mf_import_state(mf_graph *g, const int32_t *r, const int64_t *excess, const 
     MF_CUDA(cudaMemset(g->dg.stamp, 0, size_t(std::max<int64_t>(g->m, 1)) * 4));
     MF_CUDA(cudaMemset(g->dg.astamp, 0, size_t(g->n) * 4));
     MF_CUDA(cudaMemset(g->dg.rstamp, 0, size_t(g->n) * 4));
+    MF_CUDA(cudaMemset(g->dg.aq, 0, size_t(g->dg.qc) * 8));
     MF_CUDA(cudaMemcpy(&g->dg.ctl->flow, &flow, sizeof(flow), cudaMemcpyHostToDevice));
     MF_CUDA(cudaDeviceSynchronize());
     g->solved = true;
+    return MF_OK;
+}
+
+int mf_set_time_limit(mf_graph *g, int32_t time_limit_ms) {
+    if (!g || time_limit_ms < 0) return set_err(MF_EINVAL, "null graph or negative time limit");
+    g->opt.time_limit_ms = time_limit_ms;
+    g->time_limit_ns = 1000000ull * (unsigned long long)(time_limit_ms > 0 ? time_limit_ms : 60000);
     return MF_OK;
 }
 

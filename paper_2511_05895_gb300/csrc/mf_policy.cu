@@ -10,8 +10,9 @@
 //   k_mlp_grad     one thread per parameter: the gradient as a sum over the
 //                  samples in a fixed order (deterministic, no atomics);
 //   k_mlp_adam     one thread per parameter: the Adam update.
-// Loss per sample: BCE(y0, t0) + wkc * (y1 - t1)^2 / 2, averaged over the
-// mini-batch.
+// Loss per sample: BCE(y0, t0) + wkc * (y1 - t1)^2 / 2 + wmode * CE(softmax
+// of y2..y4, class t2), averaged over the mini-batch (t2 is the index of the
+// fastest processing mode, stored as a float).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -32,7 +33,8 @@ __device__ __forceinline__ float softplus(float y) { return fmaxf(y, 0.f) + log1
 __device__ __forceinline__ float sigmoid(float y) { return 1.f / (1.f + expf(-y)); }
 
 __global__ void k_mlp_fwd_bwd(const float *__restrict__ P, const float *__restrict__ X, const float *__restrict__ T0,
-                              const float *__restrict__ T1, int n, int base, int B, float wkc, float *__restrict__ W) {
+                              const float *__restrict__ T1, const float *__restrict__ T2, int n, int base, int B,
+                              float wkc, float wmode, float *__restrict__ W) {
     __shared__ float sP[kTotal];
     for (int i = threadIdx.x; i < kTotal; i += blockDim.x) sP[i] = P[i];
     __syncthreads();
@@ -44,10 +46,18 @@ __global__ void k_mlp_fwd_bwd(const float *__restrict__ P, const float *__restri
     for (int j = 0; j < kIn; ++j) x[j] = X[(size_t)idx * kIn + j];
     forward(sP, x, z, h1, h2, y);
     const float t0 = T0[idx], t1 = T1[idx];
+    const int t2 = (int)T2[idx];
     const float inv = 1.f / (float)B;
     float dy[kOut];
     dy[0] = (sigmoid(y[0]) - t0) * inv;
     dy[1] = wkc * (y[1] - t1) * inv;
+    // softmax cross-entropy of the mode logits (shifted by their maximum)
+    float mx = y[2];
+    for (int c = 1; c < kModes; ++c) mx = fmaxf(mx, y[2 + c]);
+    float se = 0.f;
+    for (int c = 0; c < kModes; ++c) se += expf(y[2 + c] - mx);
+    for (int c = 0; c < kModes; ++c) dy[2 + c] = wmode * (expf(y[2 + c] - mx) / se - (c == t2 ? 1.f : 0.f)) * inv;
+    const float ce = mx + logf(se) - y[2 + t2];
     float d2[kH2];
     for (int j = 0; j < kH2; ++j) {
         float a = 0.f;
@@ -65,10 +75,9 @@ __global__ void k_mlp_fwd_bwd(const float *__restrict__ P, const float *__restri
         row[rH2 + j] = h2[j];
         row[rD2 + j] = d2[j];
     }
-    row[rDY + 0] = dy[0];
-    row[rDY + 1] = dy[1];
+    for (int o = 0; o < kOut; ++o) row[rDY + o] = dy[o];
     const float d = y[1] - t1;
-    row[rLoss] = (softplus(y[0]) - t0 * y[0] + 0.5f * wkc * d * d) * inv;
+    row[rLoss] = (softplus(y[0]) - t0 * y[0] + 0.5f * wkc * d * d + wmode * ce) * inv;
 }
 
 // Gradient of the mini-batch loss: parameter p is one weight or bias.
@@ -136,8 +145,7 @@ __global__ void k_mlp_forward(const float *__restrict__ P, const float *__restri
     float x[kIn], z[kIn], h1[kH1], h2[kH2], y[kOut];
     for (int j = 0; j < kIn; ++j) x[j] = X[(size_t)s * kIn + j];
     forward(sP, x, z, h1, h2, y);
-    Y[(size_t)s * kOut + 0] = y[0];
-    Y[(size_t)s * kOut + 1] = y[1];
+    for (int o = 0; o < kOut; ++o) Y[(size_t)s * kOut + o] = y[o];
 }
 
 size_t workspace_bytes(int B) { return (size_t)B * kRow * sizeof(float) + (size_t)kParams * sizeof(float) + 256; }
@@ -174,21 +182,21 @@ int mf_mlp_forward(const float *P, const float *X, int32_t n, float *Y, void *st
     return cuda_rc(cudaGetLastError());
 }
 
-int mf_mlp_grad(const float *P, const float *X, const float *T0, const float *T1, int32_t n, float wkc, float *grad,
-                float *loss, void *workspace, void *stream) {
-    if (!P || !X || !T0 || !T1 || !grad || !loss || !workspace || n <= 0) return MF_EINVAL;
+int mf_mlp_grad(const float *P, const float *X, const float *T0, const float *T1, const float *T2, int32_t n,
+                float wkc, float wmode, float *grad, float *loss, void *workspace, void *stream) {
+    if (!P || !X || !T0 || !T1 || !T2 || !grad || !loss || !workspace || n <= 0) return MF_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float *W = static_cast<float *>(workspace);
-    k_mlp_fwd_bwd<<<(n + 127) / 128, 128, 0, st>>>(P, X, T0, T1, n, 0, n, wkc, W);
+    k_mlp_fwd_bwd<<<(n + 127) / 128, 128, 0, st>>>(P, X, T0, T1, T2, n, 0, n, wkc, wmode, W);
     k_mlp_grad<<<(kParams + 255) / 256, 256, 0, st>>>(W, n, grad);
     k_mlp_loss<<<1, 256, 0, st>>>(W, n, loss);
     return cuda_rc(cudaGetLastError());
 }
 
-int mf_mlp_train(float *P, float *M, float *V, const float *X, const float *T0, const float *T1, int32_t n,
-                 int32_t steps, int32_t batch, float lr, float wkc, int32_t step0, float *loss_hist, void *workspace,
-                 void *stream) {
-    if (!P || !M || !V || !X || !T0 || !T1 || !workspace || n <= 0 || steps < 0 || batch <= 0 || step0 < 0)
+int mf_mlp_train(float *P, float *M, float *V, const float *X, const float *T0, const float *T1, const float *T2,
+                 int32_t n, int32_t steps, int32_t batch, float lr, float wkc, float wmode, int32_t step0,
+                 float *loss_hist, void *workspace, void *stream) {
+    if (!P || !M || !V || !X || !T0 || !T1 || !T2 || !workspace || n <= 0 || steps < 0 || batch <= 0 || step0 < 0)
         return MF_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float *W = static_cast<float *>(workspace);
@@ -196,7 +204,7 @@ int mf_mlp_train(float *P, float *M, float *V, const float *X, const float *T0, 
     const int B = batch < n ? batch : n;
     for (int s = 0; s < steps; ++s) {
         const int base = (int)(((long long)(step0 + s) * B) % n);
-        k_mlp_fwd_bwd<<<(B + 127) / 128, 128, 0, st>>>(P, X, T0, T1, n, base, B, wkc, W);
+        k_mlp_fwd_bwd<<<(B + 127) / 128, 128, 0, st>>>(P, X, T0, T1, T2, n, base, B, wkc, wmode, W);
         k_mlp_grad<<<(kParams + 255) / 256, 256, 0, st>>>(W, B, G);
         if (loss_hist) k_mlp_loss<<<1, 256, 0, st>>>(W, B, loss_hist + s);
         const double t = (double)(step0 + s + 1);

@@ -12,12 +12,15 @@
 //     and their work overlaps on the device (each graph was created with a
 //     grid of its own size, mf_options.grid_blocks);
 //   * the device staging of the batches in flight stays within the HBM
-//     budget left after the resident graphs.
+//     budget left after the resident graphs;
+//   * a repair's grid is sized to its batch (the graph's full grid, half or
+//     a quarter of it; see grid_class), so that the CTAs left beside a large
+//     repair admit small ones.
 // Each graph has its own stream; a request is three copies of its batch into
 // the graph's device staging, the repair (the policy kernel when the graph
 // uses one, and the persistent kernel, both reading the batch size from the
-// device), captured once per graph in a CUDA graph and replayed, and the copy
-// of status and value back into pinned host memory.
+// device), captured once per graph and grid size in a CUDA graph and
+// replayed, and the copy of status and value back into pinned host memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,20 +57,32 @@ struct Result {
     double latency_us = 0;
 };
 
+// Grid classes of a repair: the graph's full grid, half and a quarter.
+constexpr int kGridClasses = 3;
+
+// The class of a request: full for recomputes and batches above 20,000
+// entries, half above 2,000, a quarter below (the repair of a small batch is
+// latency bound: a smaller grid costs it little and frees SMs).
+int grid_class(int64_t k, int32_t flags) {
+    if ((flags & MF_RECOMPUTE) || k > 20000) return 0;
+    return k > 2000 ? 1 : 2;
+}
+
 struct Slot {
     mf_graph *g = nullptr;
-    int grid = 0;
+    int grids[kGridClasses] = {0, 0, 0};   // CTAs of each grid class
     int64_t max_batch = 0;
     cudaStream_t stream = nullptr;
     int32_t *h_stage = nullptr;   // pinned: [k, pad x 3, ids[max_batch], caps[max_batch]]
     int32_t *d_stage = nullptr;   // device copy of the same layout
     int64_t *h_result = nullptr;  // pinned: status, value
     cudaEvent_t done = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraphExec_t exec_recompute = nullptr;
+    cudaGraphExec_t exec[kGridClasses] = {nullptr, nullptr, nullptr};   // repair per grid class
+    cudaGraphExec_t exec_recompute = nullptr;                          // (full grid)
     bool busy = false;
     Request cur;
     int64_t cur_bytes = 0;
+    int cur_grid = 0;
 };
 
 }  // namespace
@@ -91,6 +106,7 @@ struct mf_server {
     int64_t submitted = 0, completed = 0, failed = 0;
     int max_inflight = 0;
     int captured = 0;
+    int64_t replays = 0, direct = 0;
     std::vector<double> latencies;
     Clock::time_point t_first{}, t_last{};
     bool any = false;
@@ -125,6 +141,7 @@ bool capture(Slot &S, int32_t flags, cudaGraphExec_t *exec) {
 
 int code_of_status(int64_t bits) {
     const int32_t st = int32_t(bits & 0xffffffff);
+    if (st & 16) return MF_ECHECK;
     if (st & (2 | 4 | 8)) return MF_ETIMEOUT;
     if (st & 1) return MF_EINVAL;
     return MF_OK;
@@ -142,14 +159,18 @@ void launch_request(mf_server *S, Slot &sl, Request &&r) {
                         cudaMemcpyHostToDevice, sl.stream);
     }
     const bool rec = (r.flags & MF_RECOMPUTE) != 0;
-    cudaGraphExec_t ex = rec ? sl.exec_recompute : sl.exec;
+    const int gc = grid_class(k, r.flags);
+    cudaGraphExec_t ex = rec ? sl.exec_recompute : sl.exec[gc];
     int rc = MF_OK;
-    if (ex) {
+    if (ex && !(r.flags & MF_DELTA)) {
         if (cudaGraphLaunch(ex, sl.stream) != cudaSuccess) rc = MF_ECUDA;
+        S->replays += 1;
     } else {
+        mf_set_grid_blocks(sl.g, sl.grids[gc]);
         rc = mf_apply_updates_dev(sl.g, sl.d_stage, sl.max_batch, sl.d_stage + 4, sl.d_stage + 4 + sl.max_batch,
                                   r.flags & (MF_DELTA | MF_RECOMPUTE), sl.stream);
         if (rc == MF_OK) rc = mf_flow_value_async(sl.g, sl.h_result, sl.stream);
+        S->direct += 1;
     }
     if (rc != MF_OK) {
         cudaGetLastError();
@@ -158,8 +179,9 @@ void launch_request(mf_server *S, Slot &sl, Request &&r) {
     cudaEventRecord(sl.done, sl.stream);
     sl.busy = true;
     sl.cur_bytes = 8 * k;
+    sl.cur_grid = sl.grids[gc];
     sl.cur = std::move(r);
-    S->sm_in_use += sl.grid;
+    S->sm_in_use += sl.cur_grid;
     S->staging_in_use += sl.cur_bytes;
     S->inflight += 1;
     S->max_inflight = std::max(S->max_inflight, S->inflight);
@@ -188,7 +210,7 @@ void worker_loop(mf_server *S) {
             S->completed += 1;
             if (res.code != MF_OK) S->failed += 1;
             sl.busy = false;
-            S->sm_in_use -= sl.grid;
+            S->sm_in_use -= sl.cur_grid;
             S->staging_in_use -= sl.cur_bytes;
             S->inflight -= 1;
             progress = true;
@@ -199,7 +221,8 @@ void worker_loop(mf_server *S) {
         for (auto it = S->queue.begin(); it != S->queue.end();) {
             Slot &sl = S->slots[size_t(it->graph)];
             const int64_t bytes = 8 * int64_t(it->ids.size());
-            const bool fits = !sl.busy && S->sm_in_use + sl.grid <= S->opt.sm_slots &&
+            const int grid = sl.grids[grid_class(int64_t(it->ids.size()), it->flags)];
+            const bool fits = !sl.busy && S->sm_in_use + grid <= S->opt.sm_slots &&
                               S->staging_in_use + bytes <= S->opt.hbm_budget_bytes - S->resident_bytes;
             if (!fits) {
                 ++it;
@@ -275,7 +298,9 @@ int mf_server_add_graph(mf_server *S, mf_graph *g, int64_t max_batch, int32_t *i
     }
     Slot sl;
     sl.g = g;
-    sl.grid = grid;
+    sl.grids[0] = grid;
+    sl.grids[1] = std::max(1, grid / 2);
+    sl.grids[2] = std::max(1, grid / 4);
     sl.max_batch = max_batch;
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMallocHost(&sl.h_stage, size_t(4 * stage_words(max_batch))) != cudaSuccess ||
@@ -297,7 +322,16 @@ int mf_server_add_graph(mf_server *S, mf_graph *g, int64_t max_batch, int32_t *i
         return rc != MF_OK ? rc : MF_ECUDA;
     }
     if (S->opt.use_cuda_graphs) {
-        if (capture(sl, 0, &sl.exec)) S->captured += 1;
+        // one capture per grid class (the grid size is part of the launch
+        // captured), the recompute on the full grid
+        for (int c = kGridClasses - 1; c >= 0; --c) {
+            if (c < kGridClasses - 1 && sl.grids[c] == sl.grids[c + 1]) {
+                sl.exec[c] = sl.exec[c + 1];   // the same size: share the capture
+                continue;
+            }
+            mf_set_grid_blocks(g, sl.grids[c]);
+            if (capture(sl, 0, &sl.exec[c])) S->captured += 1;
+        }
         if (capture(sl, MF_RECOMPUTE, &sl.exec_recompute)) S->captured += 1;
     }
     S->resident_bytes += need;
@@ -349,7 +383,7 @@ int mf_server_drain(mf_server *S) {
     std::unique_lock<std::mutex> lk(S->mu);
     S->cv_work.notify_one();
     S->cv_done.wait(lk, [S] { return S->completed == S->submitted; });
-    return S->failed ? MF_ECUDA : MF_OK;
+    return MF_OK;   // each request's own code: mf_server_poll; failures are counted in the stats
 }
 
 int mf_server_stats_get(mf_server *S, mf_server_stats *out) {
@@ -362,6 +396,8 @@ int mf_server_stats_get(mf_server *S, mf_server_stats *out) {
     out->max_inflight = S->max_inflight;
     out->graphs = int32_t(S->slots.size());
     out->captured_graphs = S->captured;
+    out->replays = S->replays;
+    out->direct_launches = S->direct;
     std::vector<double> l = S->latencies;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
@@ -380,6 +416,7 @@ void mf_server_reset_stats(mf_server *S) {
     if (!S) return;
     std::lock_guard<std::mutex> lk(S->mu);
     S->latencies.clear();
+    S->replays = S->direct = 0;
     S->submitted -= S->completed;
     S->completed = 0;
     S->failed = 0;
@@ -399,7 +436,10 @@ void mf_server_destroy(mf_server *S) {
     for (auto &sl : S->slots) {
         cudaStreamSynchronize(sl.stream);
         mf_set_stream(sl.g, nullptr);   // the graph outlives the server's stream
-        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+        mf_set_grid_blocks(sl.g, sl.grids[0]);
+        for (int c = 0; c < kGridClasses; ++c)
+            if (sl.exec[c] && (c == kGridClasses - 1 || sl.exec[c] != sl.exec[c + 1]))
+                cudaGraphExecDestroy(sl.exec[c]);
         if (sl.exec_recompute) cudaGraphExecDestroy(sl.exec_recompute);
         cudaEventDestroy(sl.done);
         cudaFreeHost(sl.h_stage);

@@ -149,24 +149,67 @@ def test_push_pull_graphs_in_the_server(mf):
 
 
 def test_cuda_graph_capture_and_recompute_requests(mf):
-    g = gen.rmat(scale=12, seed=71)
+    """Every graph's repair is captured once per grid class (full, half,
+    quarter of its grid) and its recompute once; every request -- batches of
+    each class, a recompute -- is a replay of one of them, and each value is
+    the oracle's.  A delta batch is launched directly (the captures read
+    absolute capacities)."""
+    g = gen.rmat(scale=14, seed=71)
     G = mf.MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, grid_blocks=76)
     G.solve()
     G.flow_value()
     S = mf.Server()
-    S.add_graph(G, 2000)
+    S.add_graph(G, 30_000)
     st = S.stats()
+    assert st["captured_graphs"] == 4, st     # 76, 38 and 19 CTAs, plus the recompute
     cap = g.cap.copy()
     out = []
-    for j in range(4):
-        b = gen.mixed_batch(cap, 500, 1, 100, seed=71, index=j)
+    for j, k in enumerate((500, 5000, 25_000, 800)):
+        b = gen.mixed_batch(cap, k, 1, 100, seed=71, index=j)
         gen.apply_batch(cap, b)
-        t = S.submit(0, b.edge_id, b.new_cap, recompute=(j == 2))
+        t = S.submit(0, b.edge_id, b.new_cap, recompute=(j == 3))
         out.append((t, oracle.maxflow_fifo(g.n, g.row_ptr, g.col, cap, g.s, g.t)))
+    b = gen.mixed_batch(cap, 300, 1, 100, seed=71, index=9)
+    delta = (b.new_cap.astype(np.int64) - cap[b.edge_id]).astype(np.int32)
+    gen.apply_batch(cap, b)
+    out.append((S.submit(0, b.edge_id, delta, delta=True), oracle.maxflow_fifo(g.n, g.row_ptr, g.col, cap, g.s, g.t)))
     S.drain()
     for t, want in out:
-        assert S.poll(t)[1] == want
-    print("captured graphs:", st["captured_graphs"])
-    assert st["captured_graphs"] in (0, 2)
+        done, f, code, _ = S.poll(t)
+        assert done and code == 0 and f == want
+    st = S.stats()
+    assert st["replays"] == 4 and st["direct_launches"] == 1, st
     S.close()
     G.close()
+
+
+def test_small_repairs_run_beside_a_large_one(mf):
+    """With SM slots for one full grid, a small batch of another graph is
+    admitted while a large graph's big batch is in flight: its grid class is
+    a quarter of its graph's grid, which fits beside the other's half."""
+    big = gen.rmat(scale=16, seed=73)
+    small = gen.random_graph(seed=74)
+    Gb = mf.MaxFlowGraph(big.n, big.row_ptr, big.col, big.cap, big.s, big.t, grid_blocks=100)
+    Gs = mf.MaxFlowGraph(small.n, small.row_ptr, small.col, small.cap, small.s, small.t, grid_blocks=100)
+    for G in (Gb, Gs):
+        G.solve()
+        G.flow_value()
+    S = mf.Server(sm_slots=100)
+    ib, isml = S.add_graph(Gb, 20_000), S.add_graph(Gs, 100)
+    capb, caps = big.cap.copy(), small.cap.copy()
+    out = []
+    for j in range(3):
+        bb = gen.mixed_batch(capb, 10_000, 1, 500, seed=73, index=j)   # half grid (50 CTAs)
+        gen.apply_batch(capb, bb)
+        out.append((S.submit(ib, bb.edge_id, bb.new_cap), big, capb.copy()))
+        bs = gen.mixed_batch(caps, 50, 1, 50, seed=74, index=j)         # quarter grid (25 CTAs)
+        gen.apply_batch(caps, bs)
+        out.append((S.submit(isml, bs.edge_id, bs.new_cap), small, caps.copy()))
+    S.drain()
+    for t, g, c in out:
+        done, f, code, _ = S.poll(t)
+        assert done and code == 0 and f == oracle.maxflow_fifo(g.n, g.row_ptr, g.col, c, g.s, g.t)
+    assert S.stats()["max_inflight"] == 2
+    S.close()
+    Gb.close()
+    Gs.close()

@@ -376,35 +376,46 @@ def _mlp_case(seed, n=40):
     X = rng.normal(0, 1.5, (n, 12))
     T0 = (rng.uniform(size=n) < 0.5).astype(np.float64)
     T1 = rng.uniform(0, 5, n)
-    return P, X, T0, T1
+    T2 = rng.integers(0, omlp.K_MODES, n).astype(np.float64)
+    return P, X, T0, T1, T2
 
 
 def test_mlp_gradient_matches_central_differences():
-    P, X, T0, T1 = _mlp_case(1)
-    L, g = omlp.loss_and_grad(P, X, T0, T1, 0.3)
-    assert abs(L - omlp.loss(P, X, T0, T1, 0.3)) < 1e-12
+    P, X, T0, T1, T2 = _mlp_case(1)
+    L, g = omlp.loss_and_grad(P, X, T0, T1, T2, 0.3, 0.7)
+    assert abs(L - omlp.loss(P, X, T0, T1, T2, 0.3, 0.7)) < 1e-12
     rng = np.random.default_rng(2)
     idx = np.concatenate([rng.choice(omlp.N_TRAINED, 120, replace=False),
+                          np.arange(omlp.O_W3, omlp.O_B3, 13),   # weights of every output
                           np.arange(omlp.O_B3, omlp.N_TRAINED)])
     h = 1e-6
     for i in idx:
         Pp, Pm = P.copy(), P.copy()
         Pp[i] += h
         Pm[i] -= h
-        fd = (omlp.loss(Pp, X, T0, T1, 0.3) - omlp.loss(Pm, X, T0, T1, 0.3)) / (2 * h)
+        fd = (omlp.loss(Pp, X, T0, T1, T2, 0.3, 0.7) - omlp.loss(Pm, X, T0, T1, T2, 0.3, 0.7)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
 
 
 def test_mlp_closed_form_with_zero_output_weights():
     """With W3 = 0 the outputs are the biases: the loss and the gradient of b3
     have closed forms."""
-    P, X, T0, T1 = _mlp_case(3)
+    P, X, T0, T1, T2 = _mlp_case(3)
     P[omlp.O_W3:omlp.O_B3] = 0.0
     c0, c1 = 0.7, -1.2
-    P[omlp.O_B3:omlp.N_TRAINED] = [c0, c1]
-    L, g = omlp.loss_and_grad(P, X, T0, T1, 2.0)
-    want = np.log1p(np.exp(c0)) - T0.mean() * c0 + 0.5 * 2.0 * np.mean((c1 - T1) ** 2)
+    cm = np.array([0.3, -0.4, 1.1])               # the mode logits
+    P[omlp.O_B3:omlp.N_TRAINED] = [c0, c1, *cm]
+    wm = 0.5
+    L, g = omlp.loss_and_grad(P, X, T0, T1, T2, 2.0, wm)
+    # closed form of the cross-entropy of constant logits: log-sum-exp minus
+    # the mean logit of the target classes; its gradient is the softmax
+    # minus the class frequencies
+    lse = np.log(np.exp(cm).sum())
+    freq = np.array([np.mean(T2 == c) for c in range(3)])
+    want = (np.log1p(np.exp(c0)) - T0.mean() * c0 + 0.5 * 2.0 * np.mean((c1 - T1) ** 2)
+            + wm * (lse - (freq * cm).sum()))
     assert abs(L - want) < 1e-12
     assert abs(g[omlp.O_B3] - (1 / (1 + np.exp(-c0)) - T0.mean())) < 1e-12
     assert abs(g[omlp.O_B3 + 1] - 2.0 * np.mean(c1 - T1)) < 1e-12
+    assert np.allclose(g[omlp.O_B3 + 2:omlp.N_TRAINED], wm * (np.exp(cm) / np.exp(cm).sum() - freq), atol=1e-12)
     assert np.all(g[:omlp.O_W3] == 0.0)          # nothing reaches the hidden layers

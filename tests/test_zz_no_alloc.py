@@ -65,8 +65,12 @@ def regular_solve(mf, g):
 
 
 def test_noalloc_matches_regular_entry_point_twice(mf):
-    graphs = [gen.random_graph(seed=41), gen.rmat(scale=13, seed=42)]
-    for g in graphs:                       # two calls in a row share the static array
+    small, large = gen.random_graph(seed=41), gen.rmat(scale=13, seed=42)
+    # calls in a row share the static array: small, then larger, then the
+    # small graph again over what the larger call left behind (entries past
+    # the small graph's n, hub and chunk lists, queue slots)
+    graphs = [small, large, small]
+    for g in graphs:
         rc, flow, B, r, e, h = noalloc_solve(mf, g)
         assert rc == 0, mf.lib().mf_last_error()
         want = regular_solve(mf, g)
