@@ -627,16 +627,36 @@ __device__ __forceinline__ void bfs_expand_warp(const DevGraph &G, int beg, int 
 // push-pull repair (dual) a vertex of the pull side looks for a residual arc
 // w -> v from the frontier instead, and only frontier vertices of the
 // vertex's own side count.  All 32 lanes call.
-__device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base, bool dual, int L, Front &F,
-                                                    int *ccnt, Counters &K) {
+// What a lane needs of its vertex base + lane before the group's scan: its
+// height and arc range, loaded one group ahead (the warp loads the next
+// group's while it scans this one).  During a bottom-up level only the
+// owning lane writes an unvisited vertex's height, so the early read is
+// exact.
+struct BuPre {
+    int hv, beg, end;
+};
+
+__device__ __forceinline__ BuPre bu_prefetch(const DevGraph &G, int base) {
+    const int v = base + (threadIdx.x & 31);
+    BuPre p{-1, 0, 0};
+    if (v < G.n) {
+        p.hv = lcg(&G.h[v]);
+        p.beg = __ldg(&G.row[v]);
+        p.end = __ldg(&G.row[v + 1]);
+    }
+    return p;
+}
+
+__device__ __forceinline__ void bfs_bottom_up_group(const DevGraph &G, int base, const BuPre &pre, bool dual, int L,
+                                                    Front &F, int *ccnt, Counters &K) {
     const int lane = threadIdx.x & 31;
     const int n = G.n;
     const int v = base + lane;
     int beg = 0, deg = 0;
     const int side = (dual && v < n) ? G.part[v] : kPartT;
-    if (v < n && v != G.s && lcg(&G.h[v]) == n) {
-        beg = __ldg(&G.row[v]);
-        deg = __ldg(&G.row[v + 1]) - beg;
+    if (v < n && v != G.s && pre.hv == n) {
+        beg = pre.beg;
+        deg = pre.end - beg;
         if (deg > kBigDeg) {
             const int nc = (deg + kChunk - 1) / kChunk;
             const int pos = atomicAdd(ccnt, nc);
@@ -1888,8 +1908,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             if (bottom_up) {
                 // groups of 32 consecutive vertex ids (warp w: groups w, w + W, ...)
                 const int groups = (n + 31) / 32;
-                for (int grp = gwarp; grp < groups; grp += nwarps)
-                    bfs_bottom_up_group(G, grp * 32, dual, L, FR, ccnt, K);
+                BuPre pre = bu_prefetch(G, gwarp * 32);
+                for (int grp = gwarp; grp < groups; grp += nwarps) {
+                    const BuPre cur = pre;
+                    if (grp + nwarps < groups) pre = bu_prefetch(G, (grp + nwarps) * 32);
+                    bfs_bottom_up_group(G, grp * 32, cur, dual, L, FR, ccnt, K);
+                }
             } else {
                 // groups of gs frontier vertices (warp w: groups w, w + W, ...):
                 // 32, or fewer when the frontier does not fill the grid's warps,
