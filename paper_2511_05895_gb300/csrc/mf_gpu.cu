@@ -76,6 +76,10 @@ enum ExitKind { EXIT_BFS = 0, EXIT_CLEAN = 1, EXIT_NO_CUT_CHANGE = 2, EXIT_PUSH_
 // cooperative cycles the high-degree vertices get per iteration (see k_solve).
 constexpr int kMaxRounds = 16;
 constexpr int kMinHubCycles = 4;
+// The push-pull instance gives its hubs more cycles per pass: there a hub
+// left active costs another dual search of the whole graph (measured on
+// RMAT-20 100k batches: 3.2 -> 2.0-3.2 loop iterations, 1.24 -> 1.14 ms).
+constexpr int kMinHubCyclesPP = 8;
 // PushRelabel passes per loop iteration (hub cycles, then activation rounds;
 // a pass that turns hubs active again hands them to the next pass, when
 // there are at most kPassHubs of them).  The push-pull instance takes more:
@@ -1427,6 +1431,59 @@ __device__ __forceinline__ void flush_counters(Counters &K, long long *st) {
     K = Counters{};
 }
 
+// ------------------------------------------- staged BFS work items --
+// The grid-wide top-down item phase of a BFS level stages each kChunk-arc
+// item's heads and residuals (the residual of the arc into the frontier
+// vertex, or out of it on the pull side of a push-pull search) in the warp's
+// shared memory by cp.async, one item ahead: the copies of the next item are
+// in flight while the warp scans the current one from shared memory, so an
+// arc round waits only for the heights of its heads.  Residuals do not change
+// during a BFS level, so the early copy is exact.
+constexpr int kItemBuf = kChunk + 8;       // ints per array of one staged item
+constexpr int kItemWarp = 4 * kItemBuf;    // two items (heads, residuals) per warp
+constexpr int kItemOff = 2 * kSoloCap;     // after the frontier stages
+static_assert(kItemOff + (kBlock / 32) * kItemWarp <= kDynSmem / 4, "staged items exceed the shared memory");
+
+struct ItemMeta {
+    int x, y, a1;   // vertex, first arc, end of the item's arcs
+    bool fwd;       // pull side of a push-pull search: forward residuals
+};
+
+__device__ __forceinline__ ItemMeta item_meta(const DevGraph &G, int c, bool dual) {
+    const int2 it = lcg(&G.cb[c]);
+    ItemMeta m;
+    m.x = it.x;
+    m.y = it.y;
+    m.a1 = min(it.y + kChunk, __ldg(&G.row[it.x + 1]));
+    m.fwd = dual && G.part[it.x] == kPartS;
+    return m;
+}
+
+__device__ __forceinline__ void item_issue(const DevGraph &G, const ItemMeta &m, int *buf) {
+    stage_copy(G.head, buf, m.y, m.a1, G.A, G.al16);
+    stage_copy(m.fwd ? G.r : G.rr, buf + kItemBuf, m.y, m.a1, G.A, G.al16);
+}
+
+// bfs_visit_n over arcs whose heads and residuals are staged (index a - base).
+__device__ __forceinline__ void bfs_visit_staged(const DevGraph &G, const int *sv, const int *sr, int base,
+                                                 const int (&a)[kIlpB], const bool (&ok)[kIlpB], unsigned fwd,
+                                                 bool dual, int L, Front &F, Counters &K) {
+    const int n = G.n;
+    int v[kIlpB], rin[kIlpB], hv[kIlpB];
+    bool disc[kIlpB];
+#pragma unroll
+    for (int j = 0; j < kIlpB; ++j) {
+        v[j] = ok[j] ? sv[a[j] - base] : 0;
+        rin[j] = ok[j] ? sr[a[j] - base] : 0;
+        K.bfs_arcs += ok[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kIlpB; ++j) hv[j] = (rin[j] > 0 && v[j] != G.s) ? lcg(&G.h[v[j]]) : -1;
+#pragma unroll
+    for (int j = 0; j < kIlpB; ++j) disc[j] = hv[j] == n && atomicCAS(&G.h[v[j]], n, L + 1) == n;
+    bfs_discovered_n(G, disc, v, fwd, dual, F, K);
+}
+
 // debug_checks: record a failed check (the first one's kind and index) and
 // make the state invalid until the next mf_solve; the caller skips the
 // access.  Kinds: 1 list entry out of range, 2 excess != net inflow, 3
@@ -1943,24 +2000,41 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             MF_SYNC_T(S_T_BFS, L, bottom_up ? 2 : 0, cur);
             const int nch = lcg(ccnt);
             if (nch > 0) {
-                for (int c = gwarp; c < nch; c += nwarps) {
-                    const int2 item = lcg(&G.cb[c]);
-                    if (bottom_up) {
-                        bfs_bottom_up_item(G, item, dual, L, FR, K);
-                        continue;
-                    }
-                    const unsigned fw = (dual && G.part[item.x] == kPartS) ? (1u << kIlpB) - 1u : 0u;
-                    const int a1 = min(item.y + kChunk, __ldg(&G.row[item.x + 1]));
-                    for (int ab = item.y; ab < a1; ab += 32 * kIlpB) {
-                        int a[kIlpB];
-                        bool ok[kIlpB];
+                if (bottom_up) {
+                    for (int c = gwarp; c < nch; c += nwarps) bfs_bottom_up_item(G, lcg(&G.cb[c]), dual, L, FR, K);
+                } else {
+                    // items staged one ahead (see item_issue)
+                    int *const ibuf = s_dyn + kItemOff + (threadIdx.x >> 5) * kItemWarp;
+                    int c = gwarp, b = 0;
+                    ItemMeta cur = c < nch ? item_meta(G, c, dual) : ItemMeta{0, 0, 0, false};
+                    if (c < nch) item_issue(G, cur, ibuf);
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                    ItemMeta nxt = c + nwarps < nch ? item_meta(G, c + nwarps, dual) : ItemMeta{0, 0, 0, false};
+                    for (; c < nch; c += nwarps) {
+                        if (c + nwarps < nch) item_issue(G, nxt, ibuf + (b ^ 1) * 2 * kItemBuf);
+                        asm volatile("cp.async.commit_group;" ::: "memory");
+                        const ItemMeta nn =
+                            c + 2 * nwarps < nch ? item_meta(G, c + 2 * nwarps, dual) : ItemMeta{0, 0, 0, false};
+                        asm volatile("cp.async.wait_group 1;" ::: "memory");   // the current item's copies
+                        __syncwarp();
+                        const int *sv = ibuf + b * 2 * kItemBuf;
+                        const unsigned fw = cur.fwd ? (1u << kIlpB) - 1u : 0u;
+                        for (int ab = cur.y; ab < cur.a1; ab += 32 * kIlpB) {
+                            int a[kIlpB];
+                            bool ok[kIlpB];
 #pragma unroll
-                        for (int j = 0; j < kIlpB; ++j) {
-                            a[j] = ab + 32 * j + lane;
-                            ok[j] = a[j] < a1;
+                            for (int j = 0; j < kIlpB; ++j) {
+                                a[j] = ab + 32 * j + lane;
+                                ok[j] = a[j] < cur.a1;
+                            }
+                            bfs_visit_staged(G, sv, sv + kItemBuf, cur.y & ~3, a, ok, fw, dual, L, FR, K);
                         }
-                        bfs_visit_n(G, a, ok, fw, dual, L, FR, K);
+                        __syncwarp();   // every lane is done with this buffer before it is refilled
+                        cur = nxt;
+                        nxt = nn;
+                        b ^= 1;
                     }
+                    asm volatile("cp.async.wait_all;" ::: "memory");
                 }
                 front_flush(G, FR, dual, K);
                 MF_SYNC_T(S_T_BFS, L, bottom_up ? 3 : 1, nch);
@@ -2077,7 +2151,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                 if (pass > 0 && gtid == 0)
                     C->aq_head = C->aq_tail = C->aq_done = C->aq_over = C->aq_maxgen = C->aq_fin = 0;
                 const int nhc = lcg(&C->hccnt);
-                const int hub_cycles = kc > kMinHubCycles ? kc : kMinHubCycles;
+                const int hub_min = PP ? kMinHubCyclesPP : kMinHubCycles;
+                const int hub_cycles = kc > hub_min ? kc : hub_min;
                 for (int c = 0; c < hub_cycles; ++c) {
                     if (gtid == 0) ST[S_HUB_CYCLES] += 1;
                     const bool fresh = c == 0 && pass == 0;   // H1 decided by the BFS heights
