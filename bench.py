@@ -273,18 +273,25 @@ def serving_measurement(rates, duration_s: float, seed: int = 5) -> dict:
                      "max_inflight": st["max_inflight"], "captured_graphs": st["captured_graphs"],
                      "replays": st["replays"], "direct_launches": st["direct_launches"],
                      "failed": st["failed"]})
-    # every graph's final value against a fresh static solve of its final capacities
-    exact = True
+    # every graph's final value against a fresh static solve of its final
+    # capacities; where the two differ, the CPU oracle says which is right
+    exact, per_graph = True, []
     for G, g, cap in zip(Gs, graphs, caps):
         H = MaxFlowGraph(g.n, g.row_ptr, g.col, cap, g.s, g.t, kernel_cycles=4)
         H.solve()
-        exact = exact and H.flow_value() == G.flow_value()
+        served, static = G.flow_value(), H.flow_value()
         H.close()
+        row = {"graph": g.name or g.meta.get("kind", "?"), "served": served, "static": static}
+        if served != static:
+            import oracle
+            row["oracle"] = oracle.maxflow_fifo(g.n, g.row_ptr, g.col, cap, g.s, g.t)
+        exact = exact and served == static
+        per_graph.append(row)
     S.close()
     for G in Gs:
         G.close()
     return {"graphs": SERVE_GRAPHS, "mode": "push-pull", "setup_s": round(t_setup, 1), "runs": runs,
-            "final_values_equal_static_recompute": exact}
+            "final_values_equal_static_recompute": exact, "final_values": per_graph}
 
 
 def config1_measurement(seeds: int = 100) -> dict:
@@ -332,16 +339,17 @@ def config1_measurement(seeds: int = 100) -> dict:
             "values_equal_oracle": exact}
 
 
-def grid_measurement(batches: int, flush, peak: float, seed: int = 3) -> dict:
-    """The 4096 x 4096 segmentation grid (16.8M vertices, 67M n-link arcs
-    plus one s- and one t-arc per pixel): each batch rewrites the terminal
-    capacities of a random rectangle of side 64-512; dynamic repair vs static
-    GPU recompute of the same capacities (median ms), the repair's share of
-    measured HBM bandwidth, and a check that both give the same value."""
+def grid_measurement(batches: int, flush, peak: float, seed: int = 3, side: int = 4096) -> dict:
+    """The side x side segmentation grid (4096: 16.8M vertices, 67M n-link
+    arcs plus one s- and one t-arc per pixel): each batch rewrites the
+    terminal capacities of a random rectangle of side 64-512; dynamic repair
+    vs static GPU recompute of the same capacities (median ms), the repair's
+    share of measured HBM bandwidth, and a check that both give the same
+    value."""
     import torch
     from paper_2511_05895_gb300 import MaxFlowGraph
     from paper_2511_05895_gb300 import MF_MODE_PUSH_PULL
-    g = gen.grid_segmentation(4096, 4096, seed=seed)
+    g = gen.grid_segmentation(side, side, seed=seed)
     G = MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=4)
     G.solve()
     G.flow_value()
@@ -379,7 +387,7 @@ def grid_measurement(batches: int, flush, peak: float, seed: int = 3) -> dict:
     G.close()
     Gp.close()
     d, s_, pm = statistics.median(dyn), statistics.median(sta), statistics.median(ppt)
-    return {"workload": f"segmentation grid 4096^2 (n={g.n}, m={g.m}), rectangle batches of side 64-512 "
+    return {"workload": f"segmentation grid {side}^2 (n={g.n}, m={g.m}), rectangle batches of side 64-512 "
                         "rewriting terminal capacities", "batches": batches,
             "entries_median": int(statistics.median(ks)), "dynamic_ms": round(d, 3),
             "push_pull_ms": round(pm, 3), "static_recompute_ms": round(s_, 3), "speedup": round(s_ / d, 3),
@@ -462,7 +470,10 @@ def cpu_oracle_sample(g, args) -> dict:
         rp, col = os.path.join(tmp, "row_ptr.npy"), os.path.join(tmp, "col.npy")
         np.save(rp, g.row_ptr)
         np.save(col, g.col)
-        for i, b in enumerate(make_batches(cur, args.batch, cores, 0)):
+        # the batches are drawn on a copy (make_batches applies them as it
+        # draws), then applied one by one: job i sees batches 0 .. i
+        for i, b in enumerate(make_batches(cur.copy(), args.batch, cores, 0)):
+            gen.apply_batch(cur, b)
             cf = os.path.join(tmp, f"cap{i}.npy")
             np.save(cf, cur)   # the capacities after batches 0 .. i
             jobs.append((rp, col, cf, g.s, g.t))
@@ -510,7 +521,12 @@ def main():
                          "the network chooses it per batch")
     ap.add_argument("--no-pp", action="store_true", help="skip the Dynamic Push-Pull comparison")
     ap.add_argument("--size-batches", type=int, default=20, help="batches per size in the dynamic/static sweep")
-    ap.add_argument("--grid-batches", type=int, default=20, help="rectangle batches on the 4096^2 grid")
+    ap.add_argument("--grid-batches", type=int, default=20, help="rectangle batches on the segmentation grid")
+    ap.add_argument("--grid-side", type=int, default=4096, help="side of the segmentation grid")
+    ap.add_argument("--only-serve", action="store_true",
+                    help="run only the serving measurement (prints its JSON)")
+    ap.add_argument("--only-grid", action="store_true",
+                    help="run only the segmentation-grid measurement (a profiling case; prints its JSON)")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -532,6 +548,17 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2511_05895_gb300 import MaxFlowGraph, replicas
+
+    if args.only_serve:
+        print(json.dumps({"serving": serving_measurement((100.0, 300.0, 600.0, 1000.0), 3.0)}), flush=True)
+        return
+
+    if args.only_grid:
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+        peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        peak = float(json.load(open(peaks_path))["hbm_gbs"]) if os.path.exists(peaks_path) else 6800.0
+        print(json.dumps({"grid": grid_measurement(args.grid_batches, flush, peak, side=args.grid_side)}), flush=True)
+        return
 
     g = gen.rmat(scale=SCALE, seed=SEED + 1000 * rank)
     cap = g.cap.copy()

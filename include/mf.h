@@ -425,10 +425,13 @@ int mf_mlp_train(float *P, float *M, float *V, const float *X, const float *T0, 
  * all repairs in flight stay within sm_slots (so that their persistent grids
  * are co-resident and overlap), and their device staging fits the HBM budget
  * left after the resident graphs; requests that do not fit wait while later
- * ones for other graphs may start.  A request's repair runs on a grid sized
- * to its batch: the graph's full grid for batches above 20,000 entries and
- * for recomputes, half of it above 2,000 entries, a quarter below (at least
- * one CTA), so that small repairs are admitted beside large ones.  Each
+ * ones for other graphs may start (a graph's own requests keep their
+ * order).  A request's repair runs on a grid sized to its batch: the graph's
+ * full grid for batches above 20,000 entries and for recomputes, half of it
+ * above 2,000 entries, a quarter below (at least one CTA), so that small
+ * repairs are admitted beside large ones -- but graphs of 2^21 vertices or
+ * more always take their full grid and graphs of 2^19 or more at least half
+ * (every repair runs a BFS over the whole graph).  Each
  * graph's repair and recompute are captured once per grid size in CUDA
  * graphs and replayed (use_cuda_graphs; if a capture fails the server
  * launches that case directly and reports fewer captured graphs; up to six

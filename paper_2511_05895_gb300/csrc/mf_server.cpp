@@ -61,16 +61,23 @@ struct Result {
 constexpr int kGridClasses = 3;
 
 // The class of a request: full for recomputes and batches above 20,000
-// entries, half above 2,000, a quarter below (the repair of a small batch is
-// latency bound: a smaller grid costs it little and frees SMs).
-int grid_class(int64_t k, int32_t flags) {
+// entries, half above 2,000, a quarter below (the repair of a small batch on
+// a small graph is latency bound: a smaller grid costs it little and frees
+// SMs), but never smaller than the graph's size allows (max_class): every
+// repair runs at least one BFS over the whole graph, so on a graph of 2^21
+// vertices or more a smaller grid only makes it slower.
+int grid_class(int64_t k, int32_t flags, int max_class) {
     if ((flags & MF_RECOMPUTE) || k > 20000) return 0;
-    return k > 2000 ? 1 : 2;
+    const int c = k > 2000 ? 1 : 2;
+    return c < max_class ? c : max_class;
 }
+
+int graph_max_class(int32_t n) { return n >= (1 << 21) ? 0 : n >= (1 << 19) ? 1 : 2; }
 
 struct Slot {
     mf_graph *g = nullptr;
     int grids[kGridClasses] = {0, 0, 0};   // CTAs of each grid class
+    int max_class = 2;                     // smallest class the graph's size allows
     int64_t max_batch = 0;
     cudaStream_t stream = nullptr;
     int32_t *h_stage = nullptr;   // pinned: [k, pad x 3, ids[max_batch], caps[max_batch]]
@@ -108,6 +115,7 @@ struct mf_server {
     int captured = 0;
     int64_t replays = 0, direct = 0;
     std::vector<double> latencies;
+    std::vector<char> held;   // per graph: a request of it is waiting (admission scan)
     Clock::time_point t_first{}, t_last{};
     bool any = false;
     std::string err;
@@ -159,7 +167,7 @@ void launch_request(mf_server *S, Slot &sl, Request &&r) {
                         cudaMemcpyHostToDevice, sl.stream);
     }
     const bool rec = (r.flags & MF_RECOMPUTE) != 0;
-    const int gc = grid_class(k, r.flags);
+    const int gc = grid_class(k, r.flags, sl.max_class);
     cudaGraphExec_t ex = rec ? sl.exec_recompute : sl.exec[gc];
     int rc = MF_OK;
     if (ex && !(r.flags & MF_DELTA)) {
@@ -217,14 +225,19 @@ void worker_loop(mf_server *S) {
         }
         if (progress) S->cv_done.notify_all();
         // admissions, in arrival order; a request whose graph is busy or that
-        // does not fit waits while later ones may go ahead
+        // does not fit waits while later ones of other graphs may go ahead.
+        // A graph's own requests keep their order (batches carry absolute
+        // capacities): once one of them waits, the later ones wait too, even
+        // when their smaller grid would fit.
+        S->held.assign(S->slots.size(), 0);
         for (auto it = S->queue.begin(); it != S->queue.end();) {
             Slot &sl = S->slots[size_t(it->graph)];
             const int64_t bytes = 8 * int64_t(it->ids.size());
-            const int grid = sl.grids[grid_class(int64_t(it->ids.size()), it->flags)];
-            const bool fits = !sl.busy && S->sm_in_use + grid <= S->opt.sm_slots &&
+            const int grid = sl.grids[grid_class(int64_t(it->ids.size()), it->flags, sl.max_class)];
+            const bool fits = !S->held[size_t(it->graph)] && !sl.busy && S->sm_in_use + grid <= S->opt.sm_slots &&
                               S->staging_in_use + bytes <= S->opt.hbm_budget_bytes - S->resident_bytes;
             if (!fits) {
+                S->held[size_t(it->graph)] = 1;
                 ++it;
                 continue;
             }
@@ -301,6 +314,9 @@ int mf_server_add_graph(mf_server *S, mf_graph *g, int64_t max_batch, int32_t *i
     sl.grids[0] = grid;
     sl.grids[1] = std::max(1, grid / 2);
     sl.grids[2] = std::max(1, grid / 4);
+    int32_t n = 0;
+    mf_sizes(g, &n, nullptr, nullptr);
+    sl.max_class = graph_max_class(n);
     sl.max_batch = max_batch;
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMallocHost(&sl.h_stage, size_t(4 * stage_words(max_batch))) != cudaSuccess ||
@@ -324,8 +340,8 @@ int mf_server_add_graph(mf_server *S, mf_graph *g, int64_t max_batch, int32_t *i
     if (S->opt.use_cuda_graphs) {
         // one capture per grid class (the grid size is part of the launch
         // captured), the recompute on the full grid
-        for (int c = kGridClasses - 1; c >= 0; --c) {
-            if (c < kGridClasses - 1 && sl.grids[c] == sl.grids[c + 1]) {
+        for (int c = sl.max_class; c >= 0; --c) {
+            if (c < sl.max_class && sl.grids[c] == sl.grids[c + 1]) {
                 sl.exec[c] = sl.exec[c + 1];   // the same size: share the capture
                 continue;
             }
@@ -439,7 +455,7 @@ void mf_server_destroy(mf_server *S) {
         mf_set_grid_blocks(sl.g, sl.grids[0]);
         for (int c = 0; c < kGridClasses; ++c)
             if (sl.exec[c] && (c == kGridClasses - 1 || sl.exec[c] != sl.exec[c + 1]))
-                cudaGraphExecDestroy(sl.exec[c]);
+                cudaGraphExecDestroy(sl.exec[c]);   // (classes past max_class were never captured)
         if (sl.exec_recompute) cudaGraphExecDestroy(sl.exec_recompute);
         cudaEventDestroy(sl.done);
         cudaFreeHost(sl.h_stage);

@@ -213,3 +213,39 @@ def test_small_repairs_run_beside_a_large_one(mf):
     S.close()
     Gb.close()
     Gs.close()
+
+
+def test_a_graphs_requests_keep_their_order(mf):
+    """A graph's batches carry absolute capacities, so they must be applied
+    in submission order even when a later one's smaller grid would fit while
+    an earlier one waits for SMs: with SM slots for one full grid and a
+    half-grid repair of another graph in flight, a full-grid batch of graph 1
+    waits, and the small batches submitted after it must wait behind it.
+    Every value equals the oracle's on the capacities in submission order."""
+    g1, g2 = gen.rmat(scale=14, seed=75), gen.rmat(scale=14, seed=76)
+    G1 = mf.MaxFlowGraph(g1.n, g1.row_ptr, g1.col, g1.cap, g1.s, g1.t, grid_blocks=64)
+    G2 = mf.MaxFlowGraph(g2.n, g2.row_ptr, g2.col, g2.cap, g2.s, g2.t, grid_blocks=64)
+    for G in (G1, G2):
+        G.solve()
+        G.flow_value()
+    S = mf.Server(sm_slots=64)
+    try:
+        i1, i2 = S.add_graph(G1, 30_000), S.add_graph(G2, 30_000)
+        c1, c2 = g1.cap.copy(), g2.cap.copy()
+        out = []
+        for r in range(3):
+            b = gen.mixed_batch(c2, 5000, 1, 500, seed=76, index=r)       # half grid of graph 2
+            gen.apply_batch(c2, b)
+            out.append((S.submit(i2, b.edge_id, b.new_cap), g2, c2.copy()))
+            for j, k in enumerate((25_000, 300, 300)):                     # full, then quarter grids
+                b = gen.mixed_batch(c1, k, 1, 500, seed=75, index=10 * r + j)
+                gen.apply_batch(c1, b)
+                out.append((S.submit(i1, b.edge_id, b.new_cap), g1, c1.copy()))
+        S.drain()
+        for t, g, c in out:
+            done, f, code, _ = S.poll(t)
+            assert done and code == 0 and f == oracle.maxflow_fifo(g.n, g.row_ptr, g.col, c, g.s, g.t)
+    finally:
+        S.close()
+        G1.close()
+        G2.close()
