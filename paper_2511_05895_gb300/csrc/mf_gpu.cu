@@ -357,7 +357,9 @@ __device__ __forceinline__ bool grid_sync(Ctl *C) {
 
 // ---------------------------------------------------------- BFS visiting --
 // Per-thread work counters (32-bit to spare registers; added to the 64-bit
-// statistics after every loop iteration and at the end of the kernel).
+// statistics at the end of the kernel, and every 256 loop iterations so that
+// no thread's count can wrap).  Adding them once per warp after every
+// iteration cost ≈ 10 us per iteration: 3,648 atomics on each of 9 words.
 struct Counters {
     unsigned bfs_arcs = 0, bfs_verts = 0, pr_arcs = 0, push = 0, relabel = 0, ri_arcs = 0,
              ri_moves = 0, clamped = 0, resat = 0;
@@ -1431,6 +1433,39 @@ __device__ __forceinline__ void flush_counters(Counters &K, long long *st) {
     K = Counters{};
 }
 
+// The same at the end of the kernel, summed over the CTA in shared memory
+// first: one global atomic per statistic and CTA instead of one per warp.
+// Every thread of the CTA calls.
+__device__ __forceinline__ void flush_counters_cta(Counters &K, long long *st) {
+    __shared__ unsigned long long s_sum[9];
+    if (threadIdx.x < 9) s_sum[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned vals[9] = {K.bfs_verts, K.bfs_arcs, K.pr_arcs, K.push, K.relabel, K.ri_arcs, K.ri_moves,
+                              K.clamped, K.resat};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const long long v = warp_sum((long long)vals[i]);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_sum[i], (unsigned long long)v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 9 && s_sum[threadIdx.x]) {
+        int slot;
+        switch (threadIdx.x) {
+            case 0: slot = S_BFS_VERTS; break;
+            case 1: slot = S_BFS_ARCS; break;
+            case 2: slot = S_PR_ARCS; break;
+            case 3: slot = S_PUSH; break;
+            case 4: slot = S_RELABEL; break;
+            case 5: slot = S_RI_ARCS; break;
+            case 6: slot = S_RI_MOVES; break;
+            case 7: slot = S_CLAMPED; break;
+            default: slot = S_RESAT; break;
+        }
+        add_ll(&st[slot], (long long)s_sum[threadIdx.x]);
+    }
+    K = Counters{};
+}
+
 // ------------------------------------------- staged BFS work items --
 // The grid-wide top-down item phase of a BFS level stages each kChunk-arc
 // item's heads and residuals (the residual of the arc into the frontier
@@ -1794,31 +1829,41 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         }
         {
             long long dsum = 0, rdeg = 0;
-            for (long long vb = (long long)gwarp * 32; vb < n; vb += gthreads) {
-                const long long v = vb + lane;
-                bool root = false;
-                if (v < n) {
-                    const long long ev = lcg(&G.e[v]);
-                    if (stage == 0) {
-                        root = (v == t) || (v != s && ev < 0);
-                        G.h[v] = root ? 0 : n;
-                        if (root && v != t) dsum += ev;
-                    } else if (stage == 1) {
-                        // Alg. 8: h+ roots are t and the deficient vertices of T,
-                        // h- roots are s and the overflowing vertices of S (both
-                        // heights live in h: the two sides are disjoint)
-                        root = G.part[v] == kPartT ? (v == t || ev < 0) : (v == s || ev > 0);
-                        G.h[v] = root ? 0 : n;
-                    } else {
-                        // the subgraph P: its deficient vertices are the sinks;
-                        // the rest of the graph sits at n + 1, out of reach
-                        const bool inP = G.part[v] == kPartP;
-                        root = inP && ev < 0;
-                        G.h[v] = inP ? (root ? 0 : n) : n + 1;
-                    }
-                    if (root) rdeg += __ldg(&G.row[v + 1]) - __ldg(&G.row[v]);
+            constexpr int kRs = 4;   // vertices in flight per thread (their excesses loaded first)
+            for (long long vb0 = (long long)gwarp * 32; vb0 < n; vb0 += kRs * gthreads) {
+                long long evs[kRs];
+#pragma unroll
+                for (int j = 0; j < kRs; ++j) {
+                    const long long v = vb0 + j * gthreads + lane;
+                    evs[j] = v < n ? lcg(&G.e[v]) : 0;
                 }
-                warp_append(root, (int)v, &C->qcnt[0], G.qb0);
+#pragma unroll
+                for (int j = 0; j < kRs; ++j) {
+                    const long long v = vb0 + j * gthreads + lane;
+                    bool root = false;
+                    if (v < n) {
+                        const long long ev = evs[j];
+                        if (stage == 0) {
+                            root = (v == t) || (v != s && ev < 0);
+                            G.h[v] = root ? 0 : n;
+                            if (root && v != t) dsum += ev;
+                        } else if (stage == 1) {
+                            // Alg. 8: h+ roots are t and the deficient vertices of T,
+                            // h- roots are s and the overflowing vertices of S (both
+                            // heights live in h: the two sides are disjoint)
+                            root = G.part[v] == kPartT ? (v == t || ev < 0) : (v == s || ev > 0);
+                            G.h[v] = root ? 0 : n;
+                        } else {
+                            // the subgraph P: its deficient vertices are the sinks;
+                            // the rest of the graph sits at n + 1, out of reach
+                            const bool inP = G.part[v] == kPartP;
+                            root = inP && ev < 0;
+                            G.h[v] = inP ? (root ? 0 : n) : n + 1;
+                        }
+                        if (root) rdeg += __ldg(&G.row[v + 1]) - __ldg(&G.row[v]);
+                    }
+                    warp_append(root, (int)v, &C->qcnt[0], G.qb0);
+                }
             }
             dsum = warp_sum(dsum);
             rdeg = warp_sum(rdeg);
@@ -2158,7 +2203,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                     const bool fresh = c == 0 && pass == 0;   // H1 decided by the BFS heights
                     // H1: lowest residual neighbour of every unfinished hub; the
                     // warp that completes a hub's last item takes the hub's
-                    // decision (push at the lowest height, relabel, or finish)
+                    // decision (push at the lowest height, after a relabel when
+                    // the hub is not above it; or finish)
                     // the cycle's items: all hub items in cycle 0, afterwards the
                     // items of the hubs still active after the previous cycle
                     const int2 *items = c == 0 ? G.hcl : ((c - 1) & 1 ? G.hlv1 : G.hlv0);
@@ -2185,7 +2231,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                             best = pull ? hub_scan_item<true>(G, item.y, a1, beg, ptc, side, K)
                                         : hub_scan_item<false>(G, item.y, a1, beg, ptc, side, K);
                         best = warp_min(best);
-                        int decided = -2;   // -2: not the deciding warp; else the hub's mode
                         bool relabelled = false;
                         if (lane == 0) {
                             G.hikey[w] = (unsigned)(best >> 32);   // lowest height in this item
@@ -2206,47 +2251,42 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
                                     mode = -1;
                                 } else {
                                     const int hh = (int)(key >> 32);
-                                    if (hu > hh) {
-                                        mode = hh + 1;          // push to the arcs at height hh
-                                        G.hrem[i] = eu;
-                                    } else {
+                                    // push to the arcs at height hh, after
+                                    // relabelling u to hh + 1 if it is not
+                                    // above them (the same cycle's H3 pushes:
+                                    // a relabel followed by a rescan in the
+                                    // next cycle cost a cycle per relabel)
+                                    if (hu <= hh) {
                                         G.h[u] = hh + 1;
                                         ++K.relabel;
                                         relabelled = true;
-                                        mode = 0;
+                                    }
+                                    if (hh + 1 < n) {
+                                        mode = hh + 1;
+                                        G.hrem[i] = eu;
+                                    } else {
+                                        mode = -1;
                                     }
                                 }
                                 G.hmode[i] = mode;
-                                // a relabelled hub stays active; a pushing hub
-                                // is counted by H3 if it is still active after
-                                // its pushes
-                                if (mode == 0) atomicAdd(&C->hub_act[c & 1], 1);
-                                decided = mode;
+                                // (a pushing hub is counted, and listed for the
+                                // next cycle, by its last H3 item if it is still
+                                // active after its pushes)
                                 // a relabelled hub's items join the iteration's
                                 // RemoveInvalidEdges list once
                                 if (relabelled && atomicExch(&G.rstamp[u], rstamp_it) == rstamp_it)
                                     relabelled = false;
                             }
                         }
-                        // a relabelled hub takes all its items into the next
-                        // cycle's list, written by the warp that decided it (a
-                        // pushing hub is listed by its last H3 item, below)
-                        decided = __shfl_sync(kFull, decided, 0);
+                        // the deciding warp lists a newly relabelled hub's items
+                        // for RemoveInvalidEdges
                         relabelled = __shfl_sync(kFull, relabelled, 0);
-                        if (decided == 0 || relabelled) {
+                        if (relabelled) {
                             const int nit = lcg(&G.hnit[i]);
-                            int pos = 0, rpos = 0;
-                            if (lane == 0) {
-                                if (decided == 0) pos = atomicAdd(&C->hlc[c & 1], nit);
-                                if (relabelled) rpos = atomicAdd(&C->rhcnt, nit);
-                            }
-                            pos = __shfl_sync(kFull, pos, 0);
+                            int rpos = 0;
+                            if (lane == 0) rpos = atomicAdd(&C->rhcnt, nit);
                             rpos = __shfl_sync(kFull, rpos, 0);
-                            int2 *next_items = c & 1 ? G.hlv1 : G.hlv0;
-                            for (int q = lane; q < nit; q += 32) {
-                                if (decided == 0) next_items[pos + q] = make_int2(i, beg + q * kPrChunk);
-                                if (relabelled) G.hri[rpos + q] = make_int2(u, beg + q * kPrChunk);
-                            }
+                            for (int q = lane; q < nit; q += 32) G.hri[rpos + q] = make_int2(u, beg + q * kPrChunk);
                         }
                     }
                     if (!fresh) MF_SYNC_T(S_T_HUB, c, 1, nitems);
@@ -2490,7 +2530,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             }
         }
         MF_SYNC_T(S_T_RI, 0, 0, nrl + nri);
-        flush_counters(K, ST);
+        if ((it & 255) == 255) flush_counters(K, ST);
 
         // Alg. 4's loop test, on the heights PushRelabel left: no vertex is
         // active if every activation was served (the last round's list is
@@ -2590,7 +2630,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
         C->batch_err = 0;
         C->abort_loop = 0;
     }
-    flush_counters(K, ST);
+    flush_counters_cta(K, ST);
 }
 
 #undef ST
