@@ -1887,9 +1887,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
             if (cur == 0) break;
             const long long mf = lcg(&C->asum[L % 3]);
             arcs_seen += mf;
-            if (!bottom_up) bottom_up = mf * 14 > G.A - arcs_seen && cur * 64LL > n;
-            else bottom_up = cur * 24LL >= n;
             const bool dual = PP && stage == 1;   // push-pull: backward on T, forward on S
+            // (the dual search of push-pull takes a smaller vertex share: its
+            // first frontier, the overflowing and deficient vertices of both
+            // sides, is a few percent of the vertices but touches few of the
+            // others, which then scan all their arcs bottom-up)
+            if (!bottom_up) bottom_up = mf * 14 > G.A - arcs_seen && cur * (dual ? 32LL : 64LL) > n;
+            else bottom_up = cur * 24LL >= n;
             if (!bottom_up && mf <= kSoloArcs && cur <= kSoloCap) {
                 // A small frontier: CTA 0 runs the levels alone, with the
                 // frontiers in shared memory and in step by __syncthreads only,
