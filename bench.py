@@ -646,6 +646,31 @@ def main():
               "exit_kinds": sorted({st["exit_kind"] for st in psts}),
               "value_equal": Gp.flow_value() == flow_after}
 
+    # ---- the same batches under the learned batch policy --------------------
+    # (the library as a user runs it: the network picks repair or recompute,
+    # KERNELCYCLES and the mode per batch, on a graph that keeps the push-pull
+    # state so that all three modes are open)
+    learned = None
+    if not args.no_pp and args.policy == "fixed":
+        from paper_2511_05895_gb300 import MF_MODE_PUSH_PULL, MF_POLICY_LEARNED
+        from paper_2511_05895_gb300.policy import load_default_params
+        Gl = MaxFlowGraph(g.n, g.row_ptr, g.col, g.cap, g.s, g.t, kernel_cycles=args.kc, mode=MF_MODE_PUSH_PULL)
+        Gl.solve()
+        Gl.set_policy(MF_POLICY_LEARNED, load_default_params())
+        lms, lsts = time_repairs(Gl, dev, args.warmup, flush, stream)
+        l_ms = sum(lms) / len(lms)
+        learned = {"policy": "learned (MF_POLICY_LEARNED, the committed parameters)", "ms_per_step": round(l_ms, 4),
+                   "value": round(1000.0 / l_ms, 2), "unit": UNIT,
+                   "speedup_vs_headline_mode": round((1000.0 * t_total / args.steps) / l_ms, 3),
+                   "algorithmic_bytes_per_launch": int(sum(algorithmic_bytes(st, g.n) for st in lsts) / len(lsts)),
+                   "hbm_frac_of_measured": None,
+                   "choices": {"recompute": sum(st["policy_kind"] for st in lsts),
+                               "kernel_cycles": sorted({st["policy_kernel_cycles"] for st in lsts}),
+                               "modes": {name: sum(st["policy_mode"] == m for st in lsts)
+                                         for name, m in MODES.items()}},
+                   "value_equal": Gl.flow_value() == flow_after}
+        Gl.close()
+
     # ---- e2e through the C ABI with pinned host buffers ------------------
     e2e_batches = make_batches(host_cap, args.batch, args.steps, 5_000)
     pinned = [(torch.from_numpy(b.edge_id).pin_memory(), torch.from_numpy(b.new_cap).pin_memory()) for b in e2e_batches]
@@ -715,6 +740,9 @@ def main():
 
     if pp is not None:
         pp["hbm_frac_of_measured"] = round(pp["algorithmic_bytes_per_launch"] / (pp["ms_per_step"] * 1e-3) / 1e9 / peak, 4)
+    if learned is not None:
+        learned["hbm_frac_of_measured"] = round(
+            learned["algorithmic_bytes_per_launch"] / (learned["ms_per_step"] * 1e-3) / 1e9 / peak, 4)
 
     config1 = config1_measurement() if rank == 0 and not args.no_sizes else None
 
@@ -764,6 +792,7 @@ def main():
         "cpu_baseline": cpu,
         "checks": {"flow_initial": flow0, "flow_final": flow_after, "certified": certified},
         "push_pull": pp,
+        "learned_policy": learned,
         "config1": config1,
         "grid": grid,
         "serving": serving,
