@@ -146,8 +146,12 @@ typedef struct mf_options {
  *  hub_cycles   cooperative PushRelabel cycles of high-degree vertices
  *  barriers     grid barriers passed
  *  bfs_bottom_up_levels  BFS levels run bottom-up (direction-optimising)
- *  pr_rounds    PushRelabel activation rounds (vertices made active by a push
- *               are processed in the next round of the same iteration)
+ *  pr_rounds    PushRelabel activation generations: in the topology-driven
+ *               mode the rounds (a vertex made active by a push is served in
+ *               the next round of the same iteration); in the data-driven and
+ *               push-pull modes the highest generation of the activation
+ *               queue (a vertex made active is queued at once with the
+ *               pusher's generation + 1) plus one, summed over the phases
  *  policy_*     last policy decision: kind 0 = repair, 1 = recompute; the
  *               KERNELCYCLES chosen; 1 if the learned policy fell back
  *  exit_kind    how the loop ended: 0 = a BFS found no active vertex; 1 = the
@@ -487,17 +491,19 @@ void mf_server_destroy(mf_server *s);
  *          6 / 5 the barriers before and after such a run; hub
  *          cycles 0 set-up, 1 lowest-neighbour scan, 3 pushes;
  *          RemoveInvalidEdges: why the loop went on to another BFS, bits
- *          1 the activation rounds reached their cap, 2 the hub cycles
+ *          1 the activation rounds or generations reached their cap (or
+ *          the activation queue was full), 2 the hub cycles
  *          reached theirs, 4 an arc was saturated, 8 a push re-activated a
  *          high-degree vertex (0: it stopped; a height-init record of step 1,
  *          the recount of the deficits, follows)
  *   iter   loop iteration (-1 before the loop), step: BFS level, activation
- *          round or hub cycle, count: frontier size, list size or items
+ *          round (0 for a queue phase) or hub cycle, count: frontier size,
+ *          list size (queued entries for a queue phase) or items
  *   ns     device time since the previous barrier (globaltimer of CTA 0) */
 #define MF_PHASE_BATCH          0  /* batch, capacity apply, clamp, re-saturation */
 #define MF_PHASE_HEIGHT_INIT    1
 #define MF_PHASE_BFS            2
-#define MF_PHASE_PUSH_RELABEL   3  /* activation rounds, one warp per vertex        */
+#define MF_PHASE_PUSH_RELABEL   3  /* activation queue or rounds, a warp per vertex */
 #define MF_PHASE_HUB            4  /* cooperative cycles of high-degree vertices    */
 #define MF_PHASE_REMOVE_INVALID 5
 typedef struct mf_trace_rec {
