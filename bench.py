@@ -98,13 +98,19 @@ def kernel_source_hash() -> str:
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
-def recorded_traffic(kernel_hash: str):
-    """DRAM bytes per launch of k_solve from the committed ncu summary, if it
-    was taken on this exact kernel source (recorded by an earlier capture, not
-    measured in this run); else None."""
-    p = os.path.join(ROOT, "profiles", "k_solve_rmat20_batch100k.md")
+def recorded_traffic(kernel_hash: str, profile: str):
+    """DRAM bytes per launch of k_solve from the committed ncu summary
+    profiles/<profile>, if it was taken on this exact kernel source (recorded
+    by an earlier capture, not measured in this run); else None."""
+    p = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(p):
         return None
+    txt = open(p).read()
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", txt)
+    t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9]+)", txt)
+    if h and t and h.group(1) == kernel_hash:
+        return int(t.group(1))
+    return None
     txt = open(p).read()
     h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", txt)
     t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9]+)", txt)
@@ -763,7 +769,14 @@ def main():
     mean_bytes = sum(per_step_bytes) / len(per_step_bytes)
     achieved = mean_bytes / (mean_ms / 1000.0) / 1e9
     khash = kernel_source_hash()
-    traffic = recorded_traffic(khash)
+    # the capture of the workload the timed repairs ran: the data-driven
+    # repair, or the push-pull one (fixed mode, or every batch's choice);
+    # none for other modes
+    pp_steps = args.mode == "push-pull" if args.policy == "fixed" else \
+        all(c[2] == MODES["push-pull"] for c in chosen)
+    profile = "k_solve_pushpull_rmat20_batch100k.md" if pp_steps else "k_solve_rmat20_batch100k.md"
+    dd_steps = args.policy == "fixed" and args.mode == "data-driven"
+    traffic = recorded_traffic(khash, profile) if (pp_steps or dd_steps) else None
     value = world * args.steps / t_total
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -775,7 +788,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "traffic_source": ("recorded: an ncu capture of this kernel source "
-                                        "(profiles/k_solve_rmat20_batch100k.md), not measured in this run")
+                                        f"(profiles/{profile}), not measured in this run")
                      if traffic is not None else None,
                      "peak_source": peak_src, "kernel": "k_solve",
                      "algorithmic_bytes_per_launch": int(mean_bytes), "kernel_source": khash},
