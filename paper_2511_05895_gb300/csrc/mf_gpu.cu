@@ -1632,7 +1632,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_solve(DevGraph G, Job J) {
     // T = {h < n} can reach a sink, S = {h >= n} cannot
     const bool pp = PP && J.pp && pp_pick && kind == JOB_REPAIR && G.part && lcg(&C->cut_exact);
     if (pp)
-        for (long long v = gtid; v < n; v += gthreads) G.part[v] = lcg(&G.h[v]) < n ? kPartT : kPartS;
+        for (long long v0 = gtid; v0 < n; v0 += 4 * gthreads) {   // four heights in flight per thread
+            int hv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) hv[j] = v0 + j * gthreads < n ? lcg(&G.h[v0 + j * gthreads]) : 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (v0 + j * gthreads < n) G.part[v0 + j * gthreads] = hv[j] < n ? kPartT : kPartS;
+        }
 
     // ---- batch: validate, then apply (Algorithm 5) ----------------------
     bool fast = false;   // pure-increment batch that cannot change the cut
@@ -2662,6 +2669,10 @@ struct PolicyJob {
 // rule as fallback on any non-finite or out-of-range input (|z| > 8), and
 // clears the sums for the next launch.  Entries with bad ids are skipped
 // here; k_solve rejects the batch.
+// Four 256-thread CTAs per CTA of the repair's grid: a 100k-entry batch is
+// then one entry per thread, its chain of dependent gathers (edge, arc,
+// reverse arc, heads) walked once instead of three times in a row.
+constexpr int kPolicyCtasPerSlot = 4;
 __global__ void __launch_bounds__(256) k_policy(DevGraph G, PolicyJob PJ) {
     Ctl *C = G.ctl;
     if (PJ.k_dev) PJ.k = lcg(PJ.k_dev);
@@ -3005,7 +3016,7 @@ int launch_policy(mf_graph *g, int64_t k, const int *ids, const int *caps, int f
     pj.gmode = g->opt.mode;
     pj.pp_ok = g->opt.mode == MF_MODE_PUSH_PULL;
     cudaGetLastError();   // an earlier, unrelated failure of this thread is not this launch's
-    k_policy<<<g->grid, 256, 0, st>>>(g->dg, pj);
+    k_policy<<<kPolicyCtasPerSlot * g->grid, 256, 0, st>>>(g->dg, pj);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(MF_ECUDA, std::string("policy launch: ") + cudaGetErrorString(e));
     return MF_OK;
@@ -3341,7 +3352,7 @@ int mf_apply_updates_dev(mf_graph *g, const int32_t *k_dev, int64_t k_max, const
         pj.gmode = g->opt.mode;
         pj.pp_ok = g->opt.mode == MF_MODE_PUSH_PULL;
         cudaGetLastError();   // an earlier, unrelated failure of this thread is not this launch's
-        k_policy<<<g->grid, 256, 0, st>>>(g->dg, pj);
+        k_policy<<<kPolicyCtasPerSlot * g->grid, 256, 0, st>>>(g->dg, pj);
         MF_CUDA(cudaGetLastError());
         j.kind = JOB_AUTO;
     }
