@@ -177,6 +177,7 @@ struct DevGraph {
     long long A;
     int cap_limit;
     const int *row, *head, *rev, *arc_of_edge;
+    const unsigned char *edge_st;   // per edge: 1 if it leaves s or enters t (policy feature), or nullptr
     int *cap, *r, *rr, *h, *cap_edge;
     long long *e;
     unsigned *stamp;
@@ -2689,8 +2690,12 @@ __global__ void __launch_bounds__(256) k_policy(DevGraph G, PolicyJob PJ) {
         if (PJ.flags & MF_DELTA) nc = old + nc < 0 ? 0 : old + nc;
         inc += nc > old;
         sumd += nc > old ? nc - old : old - nc;
-        const int a = __ldg(&G.arc_of_edge[id]);
-        if (a >= 0 && (__ldg(&G.head[a]) == G.t || __ldg(&G.head[__ldg(&G.rev[a])]) == G.s)) ++touch;
+        if (G.edge_st) {
+            touch += __ldg(&G.edge_st[id]);
+        } else {
+            const int a = __ldg(&G.arc_of_edge[id]);
+            if (a >= 0 && (__ldg(&G.head[a]) == G.t || __ldg(&G.head[__ldg(&G.rev[a])]) == G.s)) ++touch;
+        }
     }
     inc = warp_sum(inc);
     touch = warp_sum(touch);
@@ -3190,6 +3195,8 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     D.n = n; D.s = s; D.t = t; D.m = int(m); D.A = H.arcs; D.cap_limit = H.cap_limit;
     int *row = dnew<int>(g, N + 1), *head = dnew<int>(g, A), *rev = dnew<int>(g, A), *aoe = dnew<int>(g, M);
     D.row = row; D.head = head; D.rev = rev; D.arc_of_edge = aoe;
+    unsigned char *est = dnew<unsigned char>(g, M);
+    D.edge_st = est;
     D.cap = dnew<int>(g, A); D.r = dnew<int>(g, A); D.rr = dnew<int>(g, A);
     D.h = dnew<int>(g, N); D.e = dnew<long long>(g, N);
     D.cap_edge = dnew<int>(g, M); D.stamp = dnew<unsigned>(g, M);
@@ -3220,7 +3227,7 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
     // the staging copies then fall back to plain loads
     auto al16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
     D.al16 = al16(D.head) && al16(D.r) && al16(D.rr);
-    if (!row || !head || !rev || !aoe || !D.cap || !D.r || !D.rr || !D.h || !D.e || !D.cap_edge || !D.stamp ||
+    if (!row || !head || !rev || !aoe || !est || !D.cap || !D.r || !D.rr || !D.h || !D.e || !D.cap_edge || !D.stamp ||
         !D.qb0 || !D.qb1 || !D.wl || !D.cb || !D.ctl || !g->side_buf || !D.hl || !D.hmode || !D.hkey ||
         !D.hrem || !D.hnit || !D.hdone || !D.hcl || !D.hlv0 || !D.hlv1 || !D.hikey || !D.hl2 || !D.hri || !D.astamp ||
         !D.rstamp || !D.rl || !D.aq)
@@ -3229,8 +3236,15 @@ int mf_create(int32_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, 
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
     };
     std::vector<int32_t> cap_edge(pcap, pcap + m);
+    // the policy's "edges out of s or into t" feature, one byte per edge (0
+    // for a self-loop, which has no arc)
+    std::vector<unsigned char> edge_st(size_t(std::max<int64_t>(m, 1)), 0);
+    for (int32_t u = 0; u < n; ++u)
+        for (int64_t i = prow[u]; i < prow[u + 1]; ++i)
+            edge_st[size_t(i)] = pcol[i] != u && (u == s || pcol[i] == t);
     if (up(row, H.row.data(), (N + 1) * 4) || up(head, H.head.data(), size_t(H.arcs) * 4) ||
         up(rev, H.rev.data(), size_t(H.arcs) * 4) || up(aoe, H.arc_of_edge.data(), size_t(m) * 4) ||
+        up(est, edge_st.data(), size_t(m)) ||
         up(D.cap, H.cap.data(), size_t(H.arcs) * 4) || up(D.cap_edge, cap_edge.data(), size_t(m) * 4) ||
         cudaMemsetAsync(D.stamp, 0, M * 4, st) || cudaMemsetAsync(D.ctl, 0, sizeof(Ctl), st) ||
         cudaMemsetAsync(D.aq, 0, size_t(D.qc) * 8, st) ||
@@ -3692,7 +3706,7 @@ int mf_solve_bicsr_noalloc(int32_t n, int64_t arcs, const int32_t *row, const in
     using Lo = NoAllocLayout;
     DevGraph D{};
     D.n = n; D.s = s; D.t = t; D.m = 0; D.A = arcs; D.cap_limit = 0;
-    D.row = row; D.head = head; D.rev = rev; D.arc_of_edge = nullptr;
+    D.row = row; D.head = head; D.rev = rev; D.arc_of_edge = nullptr; D.edge_st = nullptr;
     D.cap = const_cast<int *>(cap);      // read only by a solve from zero flow
     D.r = r; D.e = reinterpret_cast<long long *>(excess); D.h = height;
     D.cap_edge = nullptr; D.stamp = nullptr;
