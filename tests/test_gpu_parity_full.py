@@ -7,7 +7,8 @@
 * RMAT scale 22 with a 10k and a 100k mixed batch;
 * Dynamic Push-Pull on RMAT-20 (1k and 100k batches) and on the 4096^2
   segmentation grid (two rectangle batches);
-* the topology-driven mode on RMAT-20.
+* the topology-driven mode on RMAT-20;
+* debug_checks on RMAT-20 in the data-driven and push-pull modes.
 
 Every value is compared with the CPU oracle (FIFO push-relabel from scratch
 on the cumulative capacities, bit-exact int64) and every final state is
@@ -125,3 +126,17 @@ def test_topology_mode_rmat20(mf):
     bs, caps = sequence(g, [lambda cap: gen.mixed_batch(cap, 1000, 1, 500, seed=1, index=0),
                             lambda cap: gen.mixed_batch(cap, 100_000, 1, 500, seed=1, index=1)])
     check_sequence(mf, g, bs, caps, kernel_cycles=4, mode=mf.MF_MODE_TOPOLOGY)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", [0, 2])
+def test_debug_checks_rmat20(mf, mode):
+    """debug_checks at full size: the end-of-kernel recount of every excess,
+    residual pair and mirror entry, and the bounds checks of list entries,
+    pass on three 100k-edge batches of the benchmark graph in the
+    data-driven and the push-pull mode (a failed check makes flow_value
+    raise MF_ECHECK); every value is the oracle's."""
+    g = gen.rmat(scale=20, seed=1)
+    bs, caps = sequence(g, [lambda cap, i=i: gen.mixed_batch(cap, 100_000, 1, 500, seed=7, index=i)
+                            for i in range(3)])
+    check_sequence(mf, g, bs, caps, certify_each=False, kernel_cycles=4, mode=mode, debug_checks=True)
